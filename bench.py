@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""HPG-MxP benchmark on GB300: mixed-precision GMRES-IR GFLOP/s and time to a
+1e-9 relative residual, against the same library's FP64-only solve.
+
+One step = one full GMRES-IR solve from x0 = 0 to ||b - A x|| / ||b|| < 1e-9
+on the 128^3 workload (b = A*1 + N(0, 1e-3^2) noise, seed 0, nonsymmetric
+stencil beta = 0.5, GMRES(30), 4-level V-cycle with 1+1 symmetric
+Gauss-Seidel sweeps).  Inputs are resident in HBM when the timed region
+starts; the e2e figure repeats the solve through the C ABI with pinned host
+buffers, the copies inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+replica (the path has no data-parallel exchange on one problem), timing is
+the max over ranks and `value` sums the ranks' flops.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GMRES-IR GFLOP/s and time-to-1e-9 residual, MxP vs FP64, 1 GB300; % HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="mxp_gmres30_128cube")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=8)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def reduce_max_sum(values, op_list, backend_device=None):
+    """All-reduce a list of floats with per-entry MAX or SUM (single process:
+    identity).  Used for the max-over-ranks time and summed flops."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    out = []
+    for v, op in zip(values, op_list):
+        t = torch.tensor([float(v)], dtype=torch.float64, device=backend_device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+        out.append(float(t.item()))
+    return out
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", FALLBACK_HBM_GBS), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_sample(workload_name, iters):
+    """Times the FP64 CPU oracle on a bounded sample of the workload in a
+    child process (single-threaded BLAS): `iters` inner GMRES steps."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import hpg_oracle as O
+from workloads import WORKLOADS, x_true, rhs_noise
+w = WORKLOADS[%r]
+t0 = time.perf_counter()
+lv = O.build_hierarchy(*w.dims, levels=w.levels, beta=w.beta)
+n = lv[0].n
+b = lv[0].A @ x_true(n) + rhs_noise(n, w.noise_std, w.seed)
+t1 = time.perf_counter()
+x, info = O.gmres_ir(lv, b, tol=w.tol, restart=w.restart, maxit=%d)
+t2 = time.perf_counter()
+cyc = []
+left = info.iterations
+while left > 0:
+    cyc.append(min(left, w.restart)); left -= cyc[-1]
+fl = O.solve_flops(lv, cyc)
+print(json.dumps({"seconds": t2 - t1, "setup_s": t1 - t0, "flops": fl,
+                  "iterations": info.iterations}))
+""" % (ROOT, workload_name, iters)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from workloads import WORKLOADS
+    w = WORKLOADS[args.workload]
+    iters = max(1, args.cpu_sample_iters // 4)
+    times, flops = [], []
+    for step in range(args.warmup + args.steps):
+        r = oracle_sample(args.workload, iters)
+        if step >= args.warmup:
+            times.append(r["seconds"])
+            flops.append(r["flops"])
+    gfl = sum(flops) / sum(times) / 1e9
+    sample = ("%d inner GMRES steps of the %s workload per step (FP64 oracle, numpy/scipy, "
+              "hierarchy build untimed)" % (iters, w.name))
+    line = {"impl": "reference", "metric": METRIC, "value": gfl, "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.dims), "beta": w.beta,
+                       "restart": w.restart, "tol": w.tol},
+            "cpu_baseline": {"value": gfl, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": gfl, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_11512_gb300 as hpg
+    from paper_2507_11512_gb300 import metrics
+    from workloads import WORKLOADS, rhs_noise
+
+    w = WORKLOADS[args.workload]
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    prob = hpg.Problem(*w.dims, beta=w.beta, levels=w.levels, pre_sweeps=w.pre,
+                       post_sweeps=w.post)
+    dims_list = metrics.level_dims(w.dims, w.levels)
+    n = w.n
+    # b = A * 1 + e (FP64), formed with the library's FP64 SpMV
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    ax = prob.to_natural(prob.spmv(prob.to_storage(ones)))
+    b = ax + torch.tensor(rhs_noise(n, w.noise_std, w.seed), device=dev)
+    x = torch.zeros_like(b)
+
+    def solve(inner):
+        x.zero_()
+        return hpg.gmres_ir_solve(prob.h, b, x, tol=w.tol, restart=w.restart, maxit=w.maxit,
+                                  inner=inner)
+
+    def timed(inner, steps, warmup):
+        for _ in range(warmup):
+            solve(inner)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for _ in range(steps):
+            infos.append(solve(inner))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        return ms, infos
+
+    sampler = ClockSampler(local_rank)
+    # ---- mixed precision (headline)
+    for _ in range(args.warmup):
+        solve(hpg.HPG_FP32)
+    sampler.start()
+    ms, infos = timed(hpg.HPG_FP32, args.steps, 0)
+    clocks = sampler.stop()
+    for inf in infos:
+        assert inf["status"] == 0 and inf["rel_residual"] < w.tol, inf
+    flops = sum(metrics.solve_flops(dims_list, metrics.cycles_from_info(
+        i["iterations"], i["restarts"], w.restart)) for i in infos)
+    launches = sum(i["kernel_launches"] for i in infos)
+    ms_max, flops_sum = reduce_max_sum([ms, flops], ["max", "sum"], dev)
+    gflops = flops_sum / (ms_max / 1e3) / 1e9
+    n_ir = infos[-1]["iterations"]
+
+    # ---- FP64-only solve of the same code (Algorithm 2 as the paper's "double")
+    fp64 = None
+    if not args.no_fp64:
+        ms64, infos64 = timed(hpg.HPG_FP64, max(1, args.steps // 2), 1)
+        fl64 = sum(metrics.solve_flops(dims_list, metrics.cycles_from_info(
+            i["iterations"], i["restarts"], w.restart)) for i in infos64)
+        ms64_max, fl64_sum = reduce_max_sum([ms64, fl64], ["max", "sum"], dev)
+        n_d = infos64[-1]["iterations"]
+        fp64 = {"value": fl64_sum / (ms64_max / 1e3) / 1e9, "unit": "GFLOP/s",
+                "ms_per_solve": ms64_max / len(infos64), "iterations": n_d,
+                "rel_residual": infos64[-1]["rel_residual"]}
+
+    # ---- per-kernel profile of one MxP solve (CUDA events on the solve's stream)
+    hpg.set_profiling(prob.h, True)
+    solve(hpg.HPG_FP32)
+    torch.cuda.synchronize()
+    prof = hpg.profile_report(prob.h)
+    hpg.set_profiling(prob.h, False)
+    tot_ms = sum(p["total_ms"] for p in prof)
+    prof.sort(key=lambda p: -p["total_ms"])
+    peak, peak_src = measured_peaks()
+    top = prof[0]
+    dom_gbs = top["bytes"] / (top["total_ms"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "%s (level %d, %s)" % (
+                    top["name"], top["level"], "fp32" if top["prec"] == 1 else "fp64"),
+                "achieved": dom_gbs, "peak": peak, "unit": "GB/s", "frac": dom_gbs / peak,
+                "peak_source": peak_src, "traffic": None,
+                "launches": top["launches"], "avg_launch_us": 1e3 * top["total_ms"] / top["launches"]}
+    kernels = [{"name": p["name"], "level": p["level"], "prec": p["prec"],
+                "launches": p["launches"], "share": p["total_ms"] / tot_ms,
+                "avg_us": 1e3 * p["total_ms"] / p["launches"],
+                "gbs": (p["bytes"] / (p["total_ms"] / 1e3) / 1e9) if p["total_ms"] > 0 else 0}
+               for p in prof[:12]]
+
+    # ---- end to end through the C ABI with pinned host buffers
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    for _ in range(1):
+        xh.zero_()
+        hpg.gmres_ir_solve(prob.h, bh, xh, tol=w.tol, restart=w.restart, maxit=w.maxit,
+                           inner=hpg.HPG_FP32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_fl = 0
+    for _ in range(args.steps):
+        xh.zero_()
+        inf = hpg.gmres_ir_solve(prob.h, bh, xh, tol=w.tol, restart=w.restart, maxit=w.maxit,
+                                 inner=hpg.HPG_FP32)
+        e2e_fl += metrics.solve_flops(dims_list, metrics.cycles_from_info(
+            inf["iterations"], inf["restarts"], w.restart))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s_max, e2e_fl_sum = reduce_max_sum([e2e_s, e2e_fl], ["max", "sum"], dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(args.workload, args.cpu_sample_iters)
+        cpu = {"value": r["flops"] / r["seconds"] / 1e9, "unit": "GFLOP/s", "cores": 1,
+               "kind": "oracle",
+               "sample": "%d inner GMRES steps of %s (FP64 numpy/scipy oracle, 1 thread, "
+                         "%.1f s; hierarchy build untimed)" % (r["iterations"], w.name,
+                                                                 r["seconds"])}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.dims), "beta": w.beta,
+                       "restart": w.restart, "tol": w.tol, "levels": len(dims_list),
+                       "smoother": "1+1 symmetric multicolour Gauss-Seidel",
+                       "rhs": "A*1 + N(0, %g^2), seed %d" % (w.noise_std, w.seed),
+                       "inner": "fp32", "outer": "fp64",
+                       "l2": "inputs larger than L2 (FP32 ELL matrix %.0f MB)" % (
+                           prob.n_store() * 27 * 8 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_solution_ms": ms_max / args.steps, "iterations": n_ir,
+            "rel_residual": infos[-1]["rel_residual"],
+            "fp64": fp64,
+            "speedup_vs_fp64": (gflops / fp64["value"]) if fp64 else None,
+            "time_speedup_vs_fp64": (fp64["ms_per_solve"] / (ms_max / args.steps)) if fp64
+            else None,
+            "penalized_value": gflops * metrics.penalty(fp64["iterations"], n_ir) if fp64
+            else None,
+            "roofline": roofline, "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_fl_sum / e2e_s_max / 1e9, "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * hpgmxp.h -- C ABI of the HPG-MxP GMRES-IR solve path on one GB300 GPU.
+ *
+ * The library solves A x = b for the 27-point-stencil matrix of the HPG-MxP
+ * benchmark (arXiv 2507.11512, Sec. 2-3) with restarted GMRES(m), CGS2
+ * orthogonalisation and Givens rotations (Algorithm 3), right-preconditioned
+ * by one geometric-multigrid V-cycle (Fig. 1) whose smoother is multicolour
+ * symmetric Gauss-Seidel (eqs. (1)-(2), Sec. 3.2.1), inside an FP64
+ * iterative-refinement loop.  Every step runs in the library's CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Every call returns an int status: HPG_OK (0) or a negative HPG_ERR_*
+ *   code.  hpg_status_string() names a code; hpg_last_error() gives the
+ *   message of the most recent failure on the calling thread.
+ * - Pointers named "device" must point to memory of the current CUDA device
+ *   (cudaMalloc'd, or a torch tensor's data_ptr()); the library never frees
+ *   them.  The problem handle owns all memory the library allocates and
+ *   hpg_destroy() releases it.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued on it; calls that return results to the host
+ *   (hpg_gmres_ir_solve's info) synchronise that stream.
+ * - Grid point (i, j, k), 0 <= i < nx etc., has NATURAL index
+ *   i + nx * (j + ny * k).  Internally every level stores rows in
+ *   COLOUR-BLOCKED order: colour c = ((i+1)&1) + 2((j+1)&1) + 4((k+1)&1)
+ *   (so points with all coordinates even are colour 7), blocks c = 0..7 in
+ *   order, each block lexicographic over (i>>1, j>>1, k>>1) and padded to a
+ *   multiple of 32 rows.  hpg_spmv and hpg_mg_vcycle take vectors in this
+ *   storage order (length n_store, padding entries zero); hpg_permute
+ *   converts.  hpg_gmres_ir_solve takes natural order.
+ * - Not thread-safe per handle: calls on one handle must not overlap.
+ */
+#ifndef HPGMXP_H
+#define HPGMXP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HPG_API __attribute__((visibility("default")))
+#else
+#define HPG_API
+#endif
+
+/* ----------------------------------------------------------- status codes */
+#define HPG_OK                  0
+#define HPG_ERR_INVALID        -1  /* bad argument (size, pointer, option)      */
+#define HPG_ERR_CUDA           -2  /* a CUDA runtime call or kernel failed        */
+#define HPG_ERR_NOT_CONVERGED  -3  /* maxit reached before ||r||/||b|| < tol      */
+#define HPG_ERR_BREAKDOWN      -4  /* singular Hessenberg (H_kk = H_k+1,k = 0)    */
+#define HPG_ERR_NAN            -5  /* a residual norm became NaN or Inf           */
+#define HPG_ERR_ALLOC          -6  /* device allocation failed                    */
+#define HPG_ERR_STATE          -7  /* call out of order (e.g. no hierarchy yet)   */
+#define HPG_ERR_UNSUPPORTED    -8  /* option not built into this library          */
+
+/* -------------------------------------------------------------- precisions */
+typedef enum {
+  HPG_FP64 = 0,   /* IEEE binary64                                    */
+  HPG_FP32 = 1,   /* IEEE binary32                                    */
+  HPG_BF16 = 2,   /* bfloat16 storage (Krylov basis only), FP32 math  */
+  HPG_FP16 = 3    /* binary16 storage (Krylov basis only), FP32 math  */
+} hpg_prec;
+
+typedef struct hpg_problem hpg_problem_t;
+
+/* Stencil parameters (Sec. 3).  beta: nonsymmetric option; the off-diagonal
+ * at grid offset d = (dx,dy,dz) of the neighbour is -1 + beta*(dx+dy+dz)/3
+ * (beta = 0 is the paper's benchmarked symmetric matrix; |beta| <= 1 keeps
+ * every row weakly diagonally dominant).  theta: NULL, or nx*ny*nz FP64
+ * per-cell diagonal scales in natural order (host or device memory; copied):
+ * a_ii = 26 * theta_i.  Coarse levels inject theta: theta_c(I) = theta(2I). */
+typedef struct {
+  double beta;
+  const double* theta;
+} hpg_stencil_params;
+
+/* Geometry of one level (filled by hpg_level_info). */
+typedef struct {
+  int nx, ny, nz;
+  int64_t n;             /* grid points nx*ny*nz                              */
+  int64_t n_store;       /* rows in storage order, padding included            */
+  int64_t nnz;           /* structural non-zeros (padding slots excluded)      */
+  int64_t colour_offset[9]; /* storage start of colour block c; [8] = n_store  */
+  int64_t colour_count[8];  /* grid points of colour c                         */
+} hpg_level_desc;
+
+/* Result of a solve. */
+typedef struct {
+  int iterations;        /* total inner (Arnoldi) steps over all restarts       */
+  int restarts;          /* restart cycles completed                            */
+  int converged;         /* 1 if ||b - A x||_2 / ||b||_2 < tol (FP64)           */
+  int status;            /* same value the call returns                         */
+  double rel_residual;   /* final ||b - A x||_2 / ||b||_2, FP64                 */
+  double rho0;           /* ||b||_2                                             */
+  int kernel_launches;   /* kernels this solve enqueued (0 in graph replays)    */
+  int graph_launches;    /* CUDA graph launches this solve made                 */
+} hpg_solve_info;
+
+/* Creates a problem on the current CUDA device: the fine-level 27-point
+ * ELLPACK matrix (Sec. 3.2.2; slot-major column-index array shared by an FP64
+ * and an FP32 value array), generated on the device in storage order.
+ * Padding slots (neighbours outside the grid, Dirichlet truncation, Sec. 2)
+ * hold column = own row and value 0.
+ * nx, ny, nz >= 1 and nx*ny*nz*27 < 2^31.  p may be NULL (beta = 0).
+ * Returns HPG_ERR_INVALID for bad sizes, HPG_ERR_ALLOC / HPG_ERR_CUDA on
+ * device failure; *out is NULL on failure.  Synchronous. */
+HPG_API int hpg_setup_problem(int nx, int ny, int nz,
+                              const hpg_stencil_params* p,
+                              hpg_problem_t** out);
+
+/* Builds the geometric multigrid hierarchy (Sec. 2, Fig. 1; Sec. 3 injection
+ * restriction eq. (3), P = R^T): levels = min(levels, 1 + the number of
+ * times 2 divides nx, ny and nz together), each coarse level re-discretising
+ * the stencil on the 2x coarser grid; pre/post = symmetric Gauss-Seidel sweeps
+ * before/after the coarse correction (>= 0; the coarsest level always does
+ * one sweep).  May be called again to rebuild.  Synchronous. */
+HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels,
+                                   int pre_sweeps, int post_sweeps);
+
+/* Number of levels built (1 before hpg_build_mg_hierarchy). */
+HPG_API int hpg_num_levels(const hpg_problem_t* h, int* levels);
+
+/* Geometry of `level` (0 = finest). */
+HPG_API int hpg_level_info(const hpg_problem_t* h, int level,
+                           hpg_level_desc* out);
+
+/* Reorders a vector of `level` between natural order (length n) and storage
+ * order (length n_store).  direction 0: natural -> storage (padding entries
+ * written as 0); 1: storage -> natural.  in_prec / out_prec: HPG_FP64 or
+ * HPG_FP32 (converting on the way).  in and out are device pointers and must
+ * not overlap.  Asynchronous on `stream`. */
+HPG_API int hpg_permute(hpg_problem_t* h, int level, int direction,
+                        hpg_prec in_prec, const void* in,
+                        hpg_prec out_prec, void* out, void* stream);
+
+/* y = A_level x (Sec. 3.2.2 ELLPACK SpMV; Algorithm 3 "SpMV to get next basis
+ * vector").  prec HPG_FP64: FP64 values and vectors; HPG_FP32: FP32 values,
+ * vectors and accumulation.  x, y: device, storage order, length n_store,
+ * must not overlap.  Asynchronous on `stream`. */
+HPG_API int hpg_spmv(hpg_problem_t* h, int level, hpg_prec prec,
+                     const void* x, void* y, void* stream);
+
+/* z = M^{-1} r: one V-cycle from z = 0 starting at `level` (Fig. 1 applied
+ * recursively; Sec. 3.2.4 residual fused with restriction): per level
+ * `pre` symmetric multicolour Gauss-Seidel sweeps (forward colours 0..7,
+ * backward 7..0), fused residual-restriction to the coarse-coincident points,
+ * recursion, prolongation z_{f_c(i)} += z^c_i, `post` sweeps; the coarsest
+ * level does one sweep.  prec HPG_FP64 or HPG_FP32 (values, vectors and
+ * arithmetic).  r, z: device, storage order, length n_store, must not
+ * overlap.  Requires hpg_build_mg_hierarchy.  Asynchronous on `stream`. */
+HPG_API int hpg_mg_vcycle(hpg_problem_t* h, int level, hpg_prec prec,
+                          const void* r, void* z, void* stream);
+
+/* GMRES-IR (Algorithm 3): restarted right-preconditioned GMRES(restart) with
+ * CGS2 and Givens rotations.  The outer residual r = b - A x, its norm, the
+ * convergence test ||r||/||b|| < tol, the update x += M^{-1} Q t and the
+ * Hessenberg least-squares run in FP64; `inner` (HPG_FP32 or HPG_FP64) is the
+ * precision of the V-cycle and the Arnoldi SpMV; `basis` (HPG_FP64, HPG_FP32,
+ * HPG_BF16, HPG_FP16) the storage of the Krylov basis Q (BF16/FP16 need
+ * inner = HPG_FP32).  inner = basis = HPG_FP64 is plain FP64 GMRES
+ * (Algorithm 2).  b: FP64, natural order, n entries; x: FP64, natural order,
+ * in: initial guess, out: solution.  b and x may be device or host pointers
+ * (host buffers are staged through device memory).  restart in [1, 64],
+ * maxit >= 0 (total inner steps), tol > 0.  Returns HPG_OK on convergence,
+ * HPG_ERR_NOT_CONVERGED when maxit is reached (x holds the last iterate),
+ * HPG_ERR_NAN / HPG_ERR_BREAKDOWN on numerical failure.  b = 0 returns x = 0.
+ * info may be NULL.  Synchronises `stream`. */
+HPG_API int hpg_gmres_ir_solve(hpg_problem_t* h, const double* b, double* x,
+                               double tol, int restart, int maxit,
+                               hpg_prec inner, hpg_prec basis,
+                               hpg_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------ profiling
+ * Measurement support, not a step of the method (the paper profiles its
+ * kernels with rocprof and rocprofiler-compute, Sec. 4.3).  While enabled,
+ * every kernel the handle launches is bracketed by two CUDA events on its
+ * own stream; the report aggregates per (kernel class, level, precision)
+ * the launches, the summed event durations and the summed algorithmic DRAM
+ * bytes of the library's byte model (matrix slots, vectors read and written
+ * once).  Enabling adds two event records per launch. */
+typedef struct {
+  const char* name;      /* kernel class (static string)                 */
+  int level;             /* multigrid level (0 for vector kernels)       */
+  int prec;              /* hpg_prec of the kernel's data                */
+  long long launches;
+  double total_ms;       /* summed CUDA-event durations                  */
+  double bytes;          /* summed algorithmic DRAM bytes                */
+} hpg_kernel_stat;
+
+/* Enables (1) or disables (0) profiling and clears recorded launches. */
+HPG_API int hpg_set_profiling(hpg_problem_t* h, int enable);
+
+/* Waits for the recorded launches, writes up to `capacity` aggregated rows
+ * to out, sets *count to the number of rows available, and clears the
+ * records.  HPG_ERR_INVALID on NULL handle / count. */
+HPG_API int hpg_profile_report(hpg_problem_t* h, hpg_kernel_stat* out, int capacity,
+                               int* count);
+
+/* Frees everything the handle owns (NULL is accepted). */
+HPG_API int hpg_destroy(hpg_problem_t* h);
+
+/* Static string naming a status code. */
+HPG_API const char* hpg_status_string(int status);
+
+/* Message of the last failure on the calling thread ("" if none). */
+HPG_API const char* hpg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPGMXP_H */

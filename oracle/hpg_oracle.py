@@ -371,3 +371,18 @@ def solve_flops(levels, inner_steps_per_cycle, pre=1, post=1):
         total += kc * kc + 2 * n * kc + vc + n
     total += 2 * nnz + n + 2 * n
     return total
+
+
+# ------------------------------------------------------- single-row access --
+def stencil_row(nx, ny, nz, i, j, k, beta=0.0, theta_ijk=1.0):
+    """One matrix row by plain loops: list of (natural column, value)."""
+    row = []
+    for (dx, dy, dz) in STENCIL_OFFSETS:
+        ni, nj, nk = i + dx, j + dy, k + dz
+        if 0 <= ni < nx and 0 <= nj < ny and 0 <= nk < nz:
+            if (dx, dy, dz) == (0, 0, 0):
+                v = 26.0 * theta_ijk
+            else:
+                v = off_diagonal_value(dx, dy, dz, beta)
+            row.append((natural_index(ni, nj, nk, nx, ny), v))
+    return row

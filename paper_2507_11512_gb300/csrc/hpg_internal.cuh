@@ -1,0 +1,175 @@
+// Internal definitions of the HPG-MxP GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hpgmxp.h"
+
+namespace hpg {
+
+constexpr int kSlots = 27;        // 27-point stencil (Sec. 2)
+constexpr int kCentre = 13;       // slot of offset (0,0,0)
+constexpr int kColours = 8;       // independent sets of the 27-point stencil
+constexpr int kCoarseColour = 7;  // colour of the coarse-coincident points
+constexpr int kMaxLevels = 8;
+constexpr int kMaxRestart = 64;
+constexpr int kRowAlign = 32;     // colour blocks start on 32-row boundaries
+
+// ------------------------------------------------------------ error handling
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define HPG_CK(call)                                                     \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::hpg::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HPG_CK_LAUNCH(what)                                              \
+  do {                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                 \
+    if (e_ != cudaSuccess) return ::hpg::cuda_fail(e_, what, __FILE__, __LINE__); \
+  } while (0)
+
+// ------------------------------------------------------------------ geometry
+// Level geometry passed by value (as __grid_constant__) to every kernel that
+// maps between grid coordinates and colour-blocked storage rows.
+struct Geom {
+  int nx, ny, nz;
+  int cdx[kColours], cdy[kColours], cdz[kColours];  // colour-block extents
+  long long off[kColours + 1];                      // colour-block starts
+  long long n_store;
+};
+
+// Parity of i (resp. j, k) of the points in colour c: colour bit 0 is
+// (i+1)&1, so bit set <=> i even.
+__host__ __device__ inline int colour_parity_x(int c) { return 1 - (c & 1); }
+__host__ __device__ inline int colour_parity_y(int c) { return 1 - ((c >> 1) & 1); }
+__host__ __device__ inline int colour_parity_z(int c) { return 1 - ((c >> 2) & 1); }
+
+__host__ __device__ inline int colour_of(int i, int j, int k) {
+  return ((i + 1) & 1) | (((j + 1) & 1) << 1) | (((k + 1) & 1) << 2);
+}
+
+__host__ __device__ inline long long store_index(const Geom& g, int i, int j, int k) {
+  const int c = colour_of(i, j, k);
+  return g.off[c] + (long long)(i >> 1) +
+         (long long)g.cdx[c] * ((long long)(j >> 1) + (long long)g.cdy[c] * (k >> 1));
+}
+
+// Colour of storage row `row` (blocks are ordered by colour).
+__device__ inline int colour_of_row(const Geom& g, long long row) {
+  int c = 0;
+#pragma unroll
+  for (int q = 1; q < kColours; ++q) c += (row >= g.off[q]) ? 1 : 0;
+  return c;
+}
+
+// ------------------------------------------------------------- cached loads
+// Matrix entries are read once per sweep: stream them past L1 and mark them
+// evict-first in L2 so that the vectors stay resident.
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
+
+// ------------------------------------------------------------ host objects
+struct Level {
+  Geom g;
+  long long n = 0;        // grid points
+  long long nnz = 0;      // structural non-zeros
+  long long cnt[kColours] = {0};
+  int* cols = nullptr;    // [27][n_store]
+  float* v32 = nullptr;   // [27][n_store]
+  double* v64 = nullptr;  // [27][n_store]
+  double* theta = nullptr;  // natural order, or null
+  // V-cycle work vectors of this level (coarse levels: restricted residual and
+  // correction; every level: scratch), per precision: [0] FP64, [1] FP32.
+  void* rhs[2] = {nullptr, nullptr};
+  void* sol[2] = {nullptr, nullptr};
+};
+
+struct Workspace;   // GMRES buffers (krylov.cu)
+struct Profiler;    // per-kernel-class CUDA-event timing (profile.cu)
+
+// Kernel classes reported by the profiler.
+enum KernelClass {
+  K_GEN = 0, K_PERMUTE, K_SPMV, K_RESIDUAL, K_GS, K_RESTRICT, K_PROLONG, K_CGS2_GEMVT,
+  K_CGS2_REORTH, K_CGS2_FINAL, K_ARNOLDI_FINISH, K_TRSM, K_COMBINE, K_UPDATE_X,
+  K_CYCLE_START, K_NORM, K_NUM_CLASSES
+};
+const char* kernel_class_name(int cls);
+
+}  // namespace hpg
+
+struct hpg_problem {
+  int device = 0;
+  int num_sms = 0;
+  double beta = 0.0;
+  int nlev = 1;
+  int pre = 1, post = 1;
+  bool hierarchy = false;
+  hpg::Level lev[hpg::kMaxLevels];
+  hpg::Workspace* ws = nullptr;
+  hpg::Profiler* prof = nullptr;
+  long long launches = 0;   // kernel launches enqueued (diagnostics)
+};
+
+namespace hpg {
+
+// Profiling: when enabled, every launch is bracketed by two CUDA events on
+// its stream; prof_begin returns a slot (or -1 when disabled).
+int prof_begin(hpg_problem* h, cudaStream_t s);
+void prof_end(hpg_problem* h, int slot, int cls, int level, int prec, double bytes,
+              cudaStream_t s);
+void destroy_profiler(hpg_problem* h);
+
+// Launches `f` (a lambda that enqueues one kernel), counts it, profiles it
+// with its algorithmic DRAM bytes, and checks the launch.
+template <typename F>
+int launch(hpg_problem* h, int cls, int level, int prec, double bytes, cudaStream_t s,
+           const char* what, F&& f) {
+  const int slot = prof_begin(h, s);
+  f();
+  const cudaError_t e = cudaGetLastError();
+  prof_end(h, slot, cls, level, prec, bytes, s);
+  h->launches++;
+  if (e != cudaSuccess) return cuda_fail(e, what, __FILE__, __LINE__);
+  return HPG_OK;
+}
+
+// Allocation helpers (cudaMalloc; zero-filled).
+int dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+
+// Launchers shared between translation units.  Every one returns HPG_OK or
+// an error code and counts its launches in h->launches.
+int launch_spmv(hpg_problem* h, int level, hpg_prec prec, const void* x, void* y,
+                cudaStream_t s);
+int launch_residual64(hpg_problem* h, const double* b, const double* x, double* r,
+                      cudaStream_t s);
+int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
+               cudaStream_t s);
+int launch_permute(hpg_problem* h, int level, int direction, hpg_prec in_prec,
+                   const void* in, hpg_prec out_prec, void* out, cudaStream_t s);
+void destroy_workspace(hpg_problem* h);
+
+inline size_t prec_size(hpg_prec p) {
+  switch (p) {
+    case HPG_FP64: return 8;
+    case HPG_FP32: return 4;
+    case HPG_BF16: return 2;
+    case HPG_FP16: return 2;
+  }
+  return 0;
+}
+
+inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace hpg

@@ -1,0 +1,282 @@
+// Stencil-matrix kernels: ELLPACK SpMV, the FP64 outer residual, one colour
+// phase of multicolour Gauss-Seidel, the fused residual-restriction and the
+// injection prolongation, plus the V-cycle that strings them together.
+//
+// All kernels read the slot-major ELL arrays with streaming (evict-first)
+// loads and gather x through the read-only path; rows of one colour block are
+// contiguous, so a warp reads each slot of 32 consecutive rows as one 128-byte
+// (FP32) or 256-byte (FP64) transaction.
+
+#include "hpg_internal.cuh"
+
+namespace hpg {
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+  static constexpr int idx = 1;
+  static const float* vals(const Level& L) { return L.v32; }
+};
+template <> struct Prec<double> {
+  static constexpr int idx = 0;
+  static const double* vals(const Level& L) { return L.v64; }
+};
+
+// ------------------------------------------------------------------ kernels
+// y = A x over all storage rows (Sec. 3.2.2; Algorithm 3 SpMV).
+template <typename T>
+__global__ void __launch_bounds__(256)
+spmv_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
+            const T* __restrict__ x, T* __restrict__ y) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (row >= ns) return;
+  T acc = T(0);
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const T a = ld_stream(vals + s * ns + row);
+    const int c = ld_stream(cols + s * ns + row);
+    acc = fma(a, __ldg(x + c), acc);
+  }
+  y[row] = acc;
+}
+
+// r = b - A x in FP64 (Algorithm 3, outer residual).
+__global__ void __launch_bounds__(256)
+residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols, long long ns,
+                  const double* __restrict__ b, const double* __restrict__ x,
+                  double* __restrict__ r) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (row >= ns) return;
+  double acc = b[row];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const double a = ld_stream(vals + s * ns + row);
+    const int c = ld_stream(cols + s * ns + row);
+    acc = fma(-a, __ldg(x + c), acc);
+  }
+  r[row] = acc;
+}
+
+// One Gauss-Seidel colour phase (Sec. 3.2.1, relaxation form of eq. (1)):
+// for every row i of the colour block [row0, row0 + nrows),
+//   x_i <- (r_i - sum_{j != i} a_ij x_j) / a_ii.
+// The block is an independent set, so no row reads a value written by this
+// launch.  Entries x_j with j >= valid_end read as zero: the first forward
+// sweep from z = 0 passes valid_end = start of the current colour block, so
+// that colours not yet visited count as zero without a memset.
+template <typename T>
+__global__ void __launch_bounds__(256)
+gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
+                const T* __restrict__ r, T* x, long long row0, long long nrows,
+                long long valid_end) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nrows) return;
+  const long long row = row0 + t;
+  T acc = r[row];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    if (s == kCentre) continue;
+    const T a = ld_stream(vals + s * ns + row);
+    const int c = ld_stream(cols + s * ns + row);
+    const T xv = (c < valid_end) ? __ldg(x + c) : T(0);
+    acc = fma(-a, xv, acc);
+  }
+  const T diag = ld_stream(vals + kCentre * ns + row);
+  x[row] = acc / diag;
+}
+
+// Fused residual + injection restriction (Sec. 3.2.4, last equation):
+// rc_I = r_{f_c(I)} - sum_j A_{f_c(I) j} z_j for every coarse point I.  The
+// coarse-coincident fine points are exactly fine colour block 7, stored in the
+// same lexicographic order as the coarse grid, so threads walk that block
+// contiguously and scatter into the coarse colour blocks.
+template <typename T>
+__global__ void __launch_bounds__(256)
+restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
+                const T* __restrict__ vals, const int* __restrict__ cols,
+                const T* __restrict__ r, const T* __restrict__ z, T* __restrict__ rc) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int cx = gf.cdx[kCoarseColour], cy = gf.cdy[kCoarseColour];
+  const long long cnt = (long long)cx * cy * gf.cdz[kCoarseColour];
+  if (p >= cnt) return;
+  const long long ns = gf.n_store;
+  const long long row = gf.off[kCoarseColour] + p;
+  T acc = r[row];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const T a = ld_stream(vals + s * ns + row);
+    const int c = ld_stream(cols + s * ns + row);
+    acc = fma(-a, __ldg(z + c), acc);
+  }
+  const int I = (int)(p % cx);
+  const int J = (int)((p / cx) % cy);
+  const int K = (int)(p / ((long long)cx * cy));
+  rc[store_index(gc, I, J, K)] = acc;
+}
+
+// Prolongation P = R^T and correction (Fig. 1, eq. (3) transposed):
+// z_{f_c(I)} += zc_I.
+template <typename T>
+__global__ void __launch_bounds__(256)
+prolong_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
+               const T* __restrict__ zc, T* __restrict__ z) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int cx = gf.cdx[kCoarseColour], cy = gf.cdy[kCoarseColour];
+  const long long cnt = (long long)cx * cy * gf.cdz[kCoarseColour];
+  if (p >= cnt) return;
+  const int I = (int)(p % cx);
+  const int J = (int)((p / cx) % cy);
+  const int K = (int)(p / ((long long)cx * cy));
+  const long long row = gf.off[kCoarseColour] + p;
+  z[row] += zc[store_index(gc, I, J, K)];
+}
+
+// ----------------------------------------------------------------- launchers
+constexpr int kThreads = 256;
+
+// Algorithmic DRAM bytes per row (ELL with 27 padded slots, int32 indices;
+// every vector entry read or written once).  sv / sx: value / vector bytes.
+static double bytes_spmv_row(double sv, double sx) { return 27.0 * (sv + 4.0) + 2.0 * sx; }
+// GS phase: 27 values, 26 indices (the diagonal's is implied), r_i, the new
+// x_i, and x gathered once.
+static double bytes_gs_row(double sv, double sx) { return 27.0 * sv + 26.0 * 4.0 + 3.0 * sx; }
+static double bytes_restrict_row(double sv, double sx) { return 27.0 * (sv + 4.0) + 3.0 * sx; }
+
+template <typename T>
+static int spmv_t(hpg_problem* h, int level, const T* x, T* y, cudaStream_t s) {
+  const Level& L = h->lev[level];
+  const long long ns = L.g.n_store;
+  const T* vals = Prec<T>::vals(L);
+  return launch(h, K_SPMV, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32,
+                L.n * bytes_spmv_row(sizeof(T), sizeof(T)), s, "spmv_kernel", [&] {
+                  spmv_kernel<T><<<grid_for(ns, kThreads), kThreads, 0, s>>>(vals, L.cols, ns,
+                                                                              x, y);
+                });
+}
+
+int launch_spmv(hpg_problem* h, int level, hpg_prec prec, const void* x, void* y,
+                cudaStream_t s) {
+  if (prec == HPG_FP64) return spmv_t<double>(h, level, (const double*)x, (double*)y, s);
+  return spmv_t<float>(h, level, (const float*)x, (float*)y, s);
+}
+
+int launch_residual64(hpg_problem* h, const double* b, const double* x, double* r,
+                      cudaStream_t s) {
+  const Level& L = h->lev[0];
+  const long long ns = L.g.n_store;
+  return launch(h, K_RESIDUAL, 0, HPG_FP64, L.n * (27.0 * 12.0 + 3.0 * 8.0), s,
+                "residual64_kernel", [&] {
+                  residual64_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>(
+                      L.v64, L.cols, ns, b, x, r);
+                });
+}
+
+// State of the sweeps on one level: the colour of the most recent phase when
+// nothing else has touched the level's solution since.  A phase repeating
+// that colour would recompute identical values from identical inputs, so it
+// is skipped (it happens at the forward/backward turn and between sweeps).
+struct SweepState {
+  int last = -1;
+};
+
+template <typename T>
+static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool from_zero,
+                    SweepState& st, cudaStream_t s) {
+  if (st.last == c) return HPG_OK;
+  const Level& L = h->lev[level];
+  const long long row0 = L.g.off[c];
+  const long long nrows = L.g.off[c + 1] - row0;
+  st.last = c;
+  if (nrows == 0) return HPG_OK;
+  const long long valid_end = from_zero ? row0 : L.g.n_store;
+  const T* vals = Prec<T>::vals(L);
+  return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32,
+                L.cnt[c] * bytes_gs_row(sizeof(T), sizeof(T)), s, "gs_phase_kernel", [&] {
+                  gs_phase_kernel<T><<<grid_for(nrows, kThreads), kThreads, 0, s>>>(
+                      vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                });
+}
+
+// One symmetric Gauss-Seidel sweep (eqs. (1)-(2)): colours 0..7 then 7..0.
+template <typename T>
+static int symgs(hpg_problem* h, int level, const T* r, T* z, bool from_zero, SweepState& st,
+                 cudaStream_t s) {
+  int rc;
+  for (int c = 0; c < kColours; ++c)
+    if ((rc = gs_phase<T>(h, level, r, z, c, from_zero, st, s))) return rc;
+  for (int c = kColours - 1; c >= 0; --c)
+    if ((rc = gs_phase<T>(h, level, r, z, c, false, st, s))) return rc;
+  return HPG_OK;
+}
+
+template <typename T>
+static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
+  const Level& L = h->lev[l];
+  SweepState st;
+  int rc;
+  if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
+  if (h->pre == 0) HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
+  for (int it = 0; it < h->pre; ++it)
+    if ((rc = symgs<T>(h, l, r, z, it == 0, st, s))) return rc;
+  const Level& C = h->lev[l + 1];
+  T* rc_vec = (T*)C.rhs[Prec<T>::idx];
+  T* zc_vec = (T*)C.sol[Prec<T>::idx];
+  const long long cnt = (long long)L.g.cdx[kCoarseColour] * L.g.cdy[kCoarseColour] *
+                        L.g.cdz[kCoarseColour];
+  const int prec = Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32;
+  const T* vals = Prec<T>::vals(L);
+  rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
+              "restrict_kernel", [&] {
+                restrict_kernel<T><<<grid_for(cnt, kThreads), kThreads, 0, s>>>(
+                    L.g, C.g, vals, L.cols, r, z, rc_vec);
+              });
+  if (rc) return rc;
+  if ((rc = vcycle_t<T>(h, l + 1, rc_vec, zc_vec, s))) return rc;
+  rc = launch(h, K_PROLONG, l, prec, cnt * 3.0 * sizeof(T), s, "prolong_kernel", [&] {
+    prolong_kernel<T><<<grid_for(cnt, kThreads), kThreads, 0, s>>>(L.g, C.g, zc_vec, z);
+  });
+  if (rc) return rc;
+  st.last = -1;
+  for (int it = 0; it < h->post; ++it)
+    if ((rc = symgs<T>(h, l, r, z, false, st, s))) return rc;
+  return HPG_OK;
+}
+
+int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
+               cudaStream_t s) {
+  if (prec == HPG_FP64) return vcycle_t<double>(h, level, (const double*)r, (double*)z, s);
+  return vcycle_t<float>(h, level, (const float*)r, (float*)z, s);
+}
+
+}  // namespace hpg
+
+using namespace hpg;
+
+extern "C" {
+
+HPG_API int hpg_spmv(hpg_problem_t* h, int level, hpg_prec prec, const void* x, void* y,
+                     void* stream) {
+  if (!h || !x || !y || level < 0 || level >= h->nlev ||
+      (prec != HPG_FP64 && prec != HPG_FP32) || x == y) {
+    set_error("hpg_spmv: invalid argument (handle, level %d, prec %d, pointers)", level,
+              (int)prec);
+    return HPG_ERR_INVALID;
+  }
+  return launch_spmv(h, level, prec, x, y, (cudaStream_t)stream);
+}
+
+HPG_API int hpg_mg_vcycle(hpg_problem_t* h, int level, hpg_prec prec, const void* r, void* z,
+                          void* stream) {
+  if (!h || !r || !z || level < 0 || level >= h->nlev ||
+      (prec != HPG_FP64 && prec != HPG_FP32) || r == z) {
+    set_error("hpg_mg_vcycle: invalid argument (handle, level %d, prec %d, pointers)", level,
+              (int)prec);
+    return HPG_ERR_INVALID;
+  }
+  if (!h->hierarchy) {
+    set_error("hpg_mg_vcycle: call hpg_build_mg_hierarchy first");
+    return HPG_ERR_STATE;
+  }
+  return run_vcycle(h, level, prec, r, z, (cudaStream_t)stream);
+}
+
+}  // extern "C"
