@@ -96,8 +96,9 @@ typedef struct {
   int status;            /* same value the call returns                         */
   double rel_residual;   /* final ||b - A x||_2 / ||b||_2, FP64                 */
   double rho0;           /* ||b||_2                                             */
-  int kernel_launches;   /* kernels this solve enqueued (0 in graph replays)    */
-  int graph_launches;    /* CUDA graph launches this solve made                 */
+  int kernel_launches;   /* kernels the device ran for this solve (graph-launched
+                            kernels counted per execution)                      */
+  int graph_launches;    /* CUDA graph launches this solve made (1 or 0)        */
 } hpg_solve_info;
 
 /* Creates a problem on the current CUDA device: the fine-level 27-point

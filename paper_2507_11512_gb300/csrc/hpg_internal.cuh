@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hpgmxp.h"
@@ -76,6 +77,40 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
 
+// ---------------------------------------------- programmatic dependent launch
+// Kernels of the solve chain are launched with programmatic stream
+// serialization: the next kernel may start while its predecessor drains.
+// Every kernel calls pdl_trigger() on entry, may touch data that no earlier
+// kernel of the chain writes (the matrix) before pdl_wait(), and reads or
+// writes everything else only after pdl_wait(), which returns once all
+// prerequisite grids have completed and their writes are visible.  Without a
+// programmatic launch both are no-ops.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (no registers,
+// no completion to wait for).  p must be 16-byte aligned, bytes a multiple
+// of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// One thread of the block prefetches the block's slice [row, row + rows) of
+// the 27 value and index slots of a slot-major ELL matrix.  row and rows are
+// multiples of 4 (colour blocks start on 32-row boundaries), so every range
+// starts on a 16-byte boundary and has a multiple-of-16 size.
+template <typename TV>
+__device__ __forceinline__ void prefetch_ell_rows(const TV* vals, const int* cols, long long ns,
+                                                  long long row, int rows) {
+  if (threadIdx.x != 0 || rows <= 0) return;
+  for (int s = 0; s < 27; ++s) {
+    prefetch_l2_bulk(vals + s * ns + row, (unsigned)(rows * sizeof(TV)));
+    prefetch_l2_bulk(cols + s * ns + row, (unsigned)(rows * sizeof(int)));
+  }
+}
+
 // ------------------------------------------------------------ host objects
 struct Level {
   Geom g;
@@ -116,6 +151,9 @@ struct hpg_problem {
   hpg::Workspace* ws = nullptr;
   hpg::Profiler* prof = nullptr;
   long long launches = 0;   // kernel launches enqueued (diagnostics)
+  bool profiling = false;   // event-bracketed launches, no PDL
+  bool pdl_enabled = true;  // programmatic dependent launch on the chain
+  bool pdl_next = false;    // the previous stream operation was a kernel
 };
 
 namespace hpg {
@@ -127,16 +165,39 @@ void prof_end(hpg_problem* h, int slot, int cls, int level, int prec, double byt
               cudaStream_t s);
 void destroy_profiler(hpg_problem* h);
 
-// Launches `f` (a lambda that enqueues one kernel), counts it, profiles it
-// with its algorithmic DRAM bytes, and checks the launch.
+// Enqueues kernel<<<grid, block, 0, s>>>(args...), with the programmatic
+// serialization attribute when the previous operation on s was a kernel of
+// the chain (and not while profiling).
+template <typename... KArgs, typename... Args>
+cudaError_t kl(hpg_problem* h, void (*kern)(KArgs...), int grid, int block, cudaStream_t s,
+               Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (h->pdl_enabled && h->pdl_next && !h->profiling) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// Launches `f` (a lambda that enqueues one kernel with kl), counts it,
+// profiles it with its algorithmic DRAM bytes, and checks the launch.
 template <typename F>
 int launch(hpg_problem* h, int cls, int level, int prec, double bytes, cudaStream_t s,
            const char* what, F&& f) {
   const int slot = prof_begin(h, s);
-  f();
-  const cudaError_t e = cudaGetLastError();
+  if (slot >= 0) h->pdl_next = false;
+  const cudaError_t e0 = f();
+  const cudaError_t e = e0 != cudaSuccess ? e0 : cudaGetLastError();
   prof_end(h, slot, cls, level, prec, bytes, s);
   h->launches++;
+  h->pdl_next = true;
   if (e != cudaSuccess) return cuda_fail(e, what, __FILE__, __LINE__);
   return HPG_OK;
 }

@@ -86,6 +86,8 @@ static long long axis_pairs(int n) { return n >= 1 ? 3LL * n - 2 : 0; }
 __global__ void gen_ell_kernel(const __grid_constant__ Geom g, double beta,
                                const double* __restrict__ theta, int* __restrict__ cols,
                                double* __restrict__ v64, float* __restrict__ v32) {
+  pdl_trigger();
+  pdl_wait();
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= g.n_store) return;
   const long long ns = g.n_store;
@@ -130,6 +132,8 @@ __global__ void gen_ell_kernel(const __grid_constant__ Geom g, double beta,
 // theta of the coarse grid by injection: theta_c(I,J,K) = theta_f(2I,2J,2K).
 __global__ void inject_theta_kernel(int fnx, int fny, int cnx, int cny, int cnz,
                                     const double* __restrict__ tf, double* __restrict__ tc) {
+  pdl_trigger();
+  pdl_wait();
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long n = (long long)cnx * cny * cnz;
   if (q >= n) return;
@@ -142,6 +146,8 @@ __global__ void inject_theta_kernel(int fnx, int fny, int cnx, int cny, int cnz,
 template <typename Tin, typename Tout>
 __global__ void to_storage_kernel(const __grid_constant__ Geom g, const Tin* __restrict__ in,
                                   Tout* __restrict__ out) {
+  pdl_trigger();
+  pdl_wait();
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= g.n_store) return;
   const int c = colour_of_row(g, row);
@@ -164,6 +170,8 @@ __global__ void to_storage_kernel(const __grid_constant__ Geom g, const Tin* __r
 template <typename Tin, typename Tout>
 __global__ void to_natural_kernel(const __grid_constant__ Geom g, const Tin* __restrict__ in,
                                   Tout* __restrict__ out) {
+  pdl_trigger();
+  pdl_wait();
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long n = (long long)g.nx * g.ny * g.nz;
   if (q >= n) return;
@@ -183,8 +191,8 @@ static int build_level_matrix(hpg_problem* h, int l) {
   if ((rc = dev_alloc((void**)&L.v32, sizeof(float) * kSlots * ns))) return rc;
   return launch(h, K_GEN, l, HPG_FP64, ns * kSlots * (4.0 + 8.0 + 4.0), 0, "gen_ell_kernel",
                 [&] {
-                  gen_ell_kernel<<<grid_for(ns, 256), 256>>>(L.g, h->beta, L.theta, L.cols,
-                                                             L.v64, L.v32);
+                  return kl(h, gen_ell_kernel, grid_for(ns, 256), 256, (cudaStream_t)0, L.g,
+                            h->beta, (const double*)L.theta, L.cols, L.v64, L.v32);
                 });
 }
 
@@ -221,24 +229,29 @@ int launch_permute(hpg_problem* h, int level, int direction, hpg_prec in_prec,
     if (direction == 0) {
       const int G = grid_for(L.g.n_store, T);
       if (in_prec == HPG_FP64 && out_prec == HPG_FP64)
-        to_storage_kernel<<<G, T, 0, s>>>(L.g, (const double*)in, (double*)out);
-      else if (in_prec == HPG_FP64 && out_prec == HPG_FP32)
-        to_storage_kernel<<<G, T, 0, s>>>(L.g, (const double*)in, (float*)out);
-      else if (in_prec == HPG_FP32 && out_prec == HPG_FP64)
-        to_storage_kernel<<<G, T, 0, s>>>(L.g, (const float*)in, (double*)out);
-      else
-        to_storage_kernel<<<G, T, 0, s>>>(L.g, (const float*)in, (float*)out);
-    } else {
-      const int G = grid_for(L.n, T);
-      if (in_prec == HPG_FP64 && out_prec == HPG_FP64)
-        to_natural_kernel<<<G, T, 0, s>>>(L.g, (const double*)in, (double*)out);
-      else if (in_prec == HPG_FP64 && out_prec == HPG_FP32)
-        to_natural_kernel<<<G, T, 0, s>>>(L.g, (const double*)in, (float*)out);
-      else if (in_prec == HPG_FP32 && out_prec == HPG_FP64)
-        to_natural_kernel<<<G, T, 0, s>>>(L.g, (const float*)in, (double*)out);
-      else
-        to_natural_kernel<<<G, T, 0, s>>>(L.g, (const float*)in, (float*)out);
+        return kl(h, to_storage_kernel<double, double>, G, T, s, L.g, (const double*)in,
+                  (double*)out);
+      if (in_prec == HPG_FP64 && out_prec == HPG_FP32)
+        return kl(h, to_storage_kernel<double, float>, G, T, s, L.g, (const double*)in,
+                  (float*)out);
+      if (in_prec == HPG_FP32 && out_prec == HPG_FP64)
+        return kl(h, to_storage_kernel<float, double>, G, T, s, L.g, (const float*)in,
+                  (double*)out);
+      return kl(h, to_storage_kernel<float, float>, G, T, s, L.g, (const float*)in,
+                (float*)out);
     }
+    const int G = grid_for(L.n, T);
+    if (in_prec == HPG_FP64 && out_prec == HPG_FP64)
+      return kl(h, to_natural_kernel<double, double>, G, T, s, L.g, (const double*)in,
+                (double*)out);
+    if (in_prec == HPG_FP64 && out_prec == HPG_FP32)
+      return kl(h, to_natural_kernel<double, float>, G, T, s, L.g, (const double*)in,
+                (float*)out);
+    if (in_prec == HPG_FP32 && out_prec == HPG_FP64)
+      return kl(h, to_natural_kernel<float, double>, G, T, s, L.g, (const float*)in,
+                (double*)out);
+    return kl(h, to_natural_kernel<float, float>, G, T, s, L.g, (const float*)in,
+              (float*)out);
   });
 }
 
@@ -303,6 +316,7 @@ HPG_API int hpg_setup_problem(int nx, int ny, int nz, const hpg_stencil_params* 
   }
   h->beta = beta;
   h->nlev = 1;
+  h->pdl_next = false;
   Level& L0 = h->lev[0];
   init_level_geom(L0, nx, ny, nz);
   if (p && p->theta) {
@@ -338,6 +352,7 @@ HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels, int pre_sweeps,
               kMaxLevels, pre_sweeps, post_sweeps);
     return HPG_ERR_INVALID;
   }
+  h->pdl_next = false;
   // drop a previous hierarchy (keep level 0's matrix)
   destroy_workspace(h);
   for (int l = 0; l < h->nlev; ++l) free_level(h->lev[l], l == 0);
@@ -361,8 +376,8 @@ HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels, int pre_sweeps,
       rc = dev_alloc((void**)&C.theta, sizeof(double) * C.n);
       if (rc) break;
       rc = launch(h, K_GEN, l, HPG_FP64, 16.0 * C.n, 0, "inject_theta_kernel", [&] {
-        inject_theta_kernel<<<grid_for(C.n, 256), 256>>>(F.g.nx, F.g.ny, C.g.nx, C.g.ny, C.g.nz,
-                                                         F.theta, C.theta);
+        return kl(h, inject_theta_kernel, grid_for(C.n, 256), 256, (cudaStream_t)0, F.g.nx,
+                  F.g.ny, C.g.nx, C.g.ny, C.g.nz, (const double*)F.theta, C.theta);
       });
       if (rc) break;
     }
@@ -422,6 +437,7 @@ HPG_API int hpg_permute(hpg_problem_t* h, int level, int direction, hpg_prec in_
     set_error("hpg_permute: invalid argument");
     return HPG_ERR_INVALID;
   }
+  h->pdl_next = false;
   return launch_permute(h, level, direction, in_prec, in, out_prec, out, (cudaStream_t)stream);
 }
 

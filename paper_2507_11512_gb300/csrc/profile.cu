@@ -79,6 +79,7 @@ HPG_API int hpg_set_profiling(hpg_problem_t* h, int enable) {
   }
   if (!h->prof) h->prof = new Profiler();
   h->prof->on = enable != 0;
+  h->profiling = enable != 0;
   h->prof->used = 0;
   h->prof->recs.clear();
   return HPG_OK;

@@ -27,7 +27,11 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 spmv_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
             const T* __restrict__ x, T* __restrict__ y) {
-  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  pdl_trigger();
+  const long long row0 = blockIdx.x * (long long)blockDim.x;
+  prefetch_ell_rows(vals, cols, ns, row0, (int)min((long long)blockDim.x, ns - row0));
+  pdl_wait();
+  const long long row = row0 + threadIdx.x;
   if (row >= ns) return;
   T acc = T(0);
 #pragma unroll
@@ -44,7 +48,11 @@ __global__ void __launch_bounds__(256)
 residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols, long long ns,
                   const double* __restrict__ b, const double* __restrict__ x,
                   double* __restrict__ r) {
-  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  pdl_trigger();
+  const long long row0 = blockIdx.x * (long long)blockDim.x;
+  prefetch_ell_rows(vals, cols, ns, row0, (int)min((long long)blockDim.x, ns - row0));
+  pdl_wait();
+  const long long row = row0 + threadIdx.x;
   if (row >= ns) return;
   double acc = b[row];
 #pragma unroll
@@ -68,7 +76,11 @@ __global__ void __launch_bounds__(256)
 gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                 const T* __restrict__ r, T* x, long long row0, long long nrows,
                 long long valid_end) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  pdl_trigger();
+  const long long t0 = blockIdx.x * (long long)blockDim.x;
+  prefetch_ell_rows(vals, cols, ns, row0 + t0, (int)min((long long)blockDim.x, nrows - t0));
+  pdl_wait();
+  const long long t = t0 + threadIdx.x;
   if (t >= nrows) return;
   const long long row = row0 + t;
   T acc = r[row];
@@ -94,11 +106,18 @@ __global__ void __launch_bounds__(256)
 restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                 const T* __restrict__ vals, const int* __restrict__ cols,
                 const T* __restrict__ r, const T* __restrict__ z, T* __restrict__ rc) {
-  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  pdl_trigger();
   const int cx = gf.cdx[kCoarseColour], cy = gf.cdy[kCoarseColour];
   const long long cnt = (long long)cx * cy * gf.cdz[kCoarseColour];
-  if (p >= cnt) return;
   const long long ns = gf.n_store;
+  const long long p0 = blockIdx.x * (long long)blockDim.x;
+  // rows of the (32-row aligned) colour block, padded tail included
+  const long long nblk = gf.off[kCoarseColour + 1] - gf.off[kCoarseColour];
+  prefetch_ell_rows(vals, cols, ns, gf.off[kCoarseColour] + p0,
+                    (int)min((long long)blockDim.x, nblk - p0));
+  pdl_wait();
+  const long long p = p0 + threadIdx.x;
+  if (p >= cnt) return;
   const long long row = gf.off[kCoarseColour] + p;
   T acc = r[row];
 #pragma unroll
@@ -119,6 +138,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 prolong_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                const T* __restrict__ zc, T* __restrict__ z) {
+  pdl_trigger();
+  pdl_wait();
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int cx = gf.cdx[kCoarseColour], cy = gf.cdy[kCoarseColour];
   const long long cnt = (long long)cx * cy * gf.cdz[kCoarseColour];
@@ -148,8 +169,8 @@ static int spmv_t(hpg_problem* h, int level, const T* x, T* y, cudaStream_t s) {
   const T* vals = Prec<T>::vals(L);
   return launch(h, K_SPMV, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32,
                 L.n * bytes_spmv_row(sizeof(T), sizeof(T)), s, "spmv_kernel", [&] {
-                  spmv_kernel<T><<<grid_for(ns, kThreads), kThreads, 0, s>>>(vals, L.cols, ns,
-                                                                              x, y);
+                  return kl(h, spmv_kernel<T>, grid_for(ns, kThreads), kThreads, s, vals, L.cols,
+                            ns, x, y);
                 });
 }
 
@@ -165,8 +186,8 @@ int launch_residual64(hpg_problem* h, const double* b, const double* x, double* 
   const long long ns = L.g.n_store;
   return launch(h, K_RESIDUAL, 0, HPG_FP64, L.n * (27.0 * 12.0 + 3.0 * 8.0), s,
                 "residual64_kernel", [&] {
-                  residual64_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>(
-                      L.v64, L.cols, ns, b, x, r);
+                  return kl(h, residual64_kernel, grid_for(ns, kThreads), kThreads, s, L.v64,
+                            L.cols, ns, b, x, r);
                 });
 }
 
@@ -191,8 +212,8 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
   const T* vals = Prec<T>::vals(L);
   return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32,
                 L.cnt[c] * bytes_gs_row(sizeof(T), sizeof(T)), s, "gs_phase_kernel", [&] {
-                  gs_phase_kernel<T><<<grid_for(nrows, kThreads), kThreads, 0, s>>>(
-                      vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                  return kl(h, gs_phase_kernel<T>, grid_for(nrows, kThreads), kThreads, s, vals,
+                            L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
                 });
 }
 
@@ -214,7 +235,10 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   SweepState st;
   int rc;
   if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
-  if (h->pre == 0) HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
+  if (h->pre == 0) {
+    HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
+    h->pdl_next = false;
+  }
   for (int it = 0; it < h->pre; ++it)
     if ((rc = symgs<T>(h, l, r, z, it == 0, st, s))) return rc;
   const Level& C = h->lev[l + 1];
@@ -226,13 +250,14 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   const T* vals = Prec<T>::vals(L);
   rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
               "restrict_kernel", [&] {
-                restrict_kernel<T><<<grid_for(cnt, kThreads), kThreads, 0, s>>>(
-                    L.g, C.g, vals, L.cols, r, z, rc_vec);
+                return kl(h, restrict_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
+                          vals, L.cols, r, z, rc_vec);
               });
   if (rc) return rc;
   if ((rc = vcycle_t<T>(h, l + 1, rc_vec, zc_vec, s))) return rc;
   rc = launch(h, K_PROLONG, l, prec, cnt * 3.0 * sizeof(T), s, "prolong_kernel", [&] {
-    prolong_kernel<T><<<grid_for(cnt, kThreads), kThreads, 0, s>>>(L.g, C.g, zc_vec, z);
+    return kl(h, prolong_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
+              (const T*)zc_vec, z);
   });
   if (rc) return rc;
   st.last = -1;
@@ -261,6 +286,7 @@ HPG_API int hpg_spmv(hpg_problem_t* h, int level, hpg_prec prec, const void* x, 
               (int)prec);
     return HPG_ERR_INVALID;
   }
+  h->pdl_next = false;
   return launch_spmv(h, level, prec, x, y, (cudaStream_t)stream);
 }
 
@@ -276,6 +302,7 @@ HPG_API int hpg_mg_vcycle(hpg_problem_t* h, int level, hpg_prec prec, const void
     set_error("hpg_mg_vcycle: call hpg_build_mg_hierarchy first");
     return HPG_ERR_STATE;
   }
+  h->pdl_next = false;
   return run_vcycle(h, level, prec, r, z, (cudaStream_t)stream);
 }
 

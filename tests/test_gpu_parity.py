@@ -251,3 +251,49 @@ def test_theta_scaled_diagonal():
                            L.dims)
             ref = O.vcycle(lv, r, l)
             assert np.abs(z - ref).max() <= FP64_REL * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("inner", [hpg.HPG_FP32, hpg.HPG_FP64])
+def test_graph_and_eager_paths_agree(inner):
+    # the whole-solve CUDA graph (conditional WHILE/IF nodes, programmatic
+    # launches) and the host-driven path run the same deterministic kernels
+    dims, beta = (24, 20, 28), 0.5
+    lv = oracle_hierarchy(dims, 4, beta)
+    n = lv[0].n
+    b = lv[0].A @ x_true(n) + rhs_noise(n, 1e-3, seed=0)
+    with hpg.Problem(*dims, beta=beta) as p:
+        bt = gpu(b, torch.float64)
+        xg = torch.zeros_like(bt)
+        ig = hpg.gmres_ir_solve(p.h, bt, xg, tol=1e-10, restart=12, inner=inner)
+        hpg.set_profiling(p.h, True)
+        xe = torch.zeros_like(bt)
+        ie = hpg.gmres_ir_solve(p.h, bt, xe, tol=1e-10, restart=12, inner=inner)
+        rep = hpg.profile_report(p.h)
+        hpg.set_profiling(p.h, False)
+    assert ig["graph_launches"] == 1 and ie["graph_launches"] == 0
+    assert ig["iterations"] == ie["iterations"] and ig["restarts"] == ie["restarts"]
+    assert ig["kernel_launches"] == ie["kernel_launches"]
+    torch.testing.assert_close(xg, xe, rtol=0, atol=0)
+    names = {r["name"] for r in rep}
+    assert {"gs_colour_phase", "spmv", "cgs2_gemvt", "cgs2_reorth", "cgs2_final_norm",
+            "arnoldi_finish_givens", "restrict", "prolong", "residual_fp64"} <= names
+    gs0 = [r for r in rep if r["name"] == "gs_colour_phase" and r["level"] == 0][0]
+    assert gs0["launches"] == (ie["iterations"] + ie["restarts"]) * 30
+    assert gs0["total_ms"] > 0 and gs0["bytes"] > 0
+
+
+def test_repeated_solves_recapture():
+    dims = (16, 16, 16)
+    lv = oracle_hierarchy(dims, 4, 0.5)
+    b = lv[0].A @ x_true(lv[0].n)
+    with hpg.Problem(*dims, beta=0.5) as p:
+        bt = gpu(b, torch.float64)
+        res = []
+        for restart, inner in [(30, hpg.HPG_FP32), (10, hpg.HPG_FP32), (30, hpg.HPG_FP64),
+                               (30, hpg.HPG_FP32), (30, hpg.HPG_FP32)]:
+            x = torch.zeros_like(bt)
+            info = hpg.gmres_ir_solve(p.h, bt, x, restart=restart, inner=inner)
+            assert info["status"] == 0 and info["rel_residual"] < 1e-9
+            res.append(x.cpu().numpy())
+        np.testing.assert_array_equal(res[0], res[3])
+        np.testing.assert_array_equal(res[3], res[4])
