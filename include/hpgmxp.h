@@ -201,6 +201,16 @@ HPG_API int hpg_set_profiling(hpg_problem_t* h, int enable);
 HPG_API int hpg_profile_report(hpg_problem_t* h, hpg_kernel_stat* out, int capacity,
                                int* count);
 
+/* Execution of hpg_gmres_ir_solve.  HPG_EXEC_GRAPH (default): the whole solve
+ * runs as one CUDA graph with conditional WHILE / IF nodes (one launch, one
+ * host synchronisation).  HPG_EXEC_EAGER: the same kernels driven from the
+ * host, one synchronisation per inner step (for tools that cannot look into
+ * conditional graphs).  Both give bitwise-identical results.  Enabling
+ * profiling implies eager execution. */
+#define HPG_EXEC_GRAPH 0
+#define HPG_EXEC_EAGER 1
+HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
+
 /* Frees everything the handle owns (NULL is accepted). */
 HPG_API int hpg_destroy(hpg_problem_t* h);
 

@@ -11,11 +11,12 @@ import ctypes
 
 from ._lib import (HPG_BF16, HPG_ERR_ALLOC, HPG_ERR_BREAKDOWN, HPG_ERR_CUDA,  # noqa: F401
                    HPG_ERR_INVALID, HPG_ERR_NAN, HPG_ERR_NOT_CONVERGED, HPG_ERR_STATE,
-                   HPG_ERR_UNSUPPORTED, HPG_FP16, HPG_FP32, HPG_FP64, HPG_OK, HpgError,
+                   HPG_ERR_UNSUPPORTED, HPG_EXEC_EAGER, HPG_EXEC_GRAPH, HPG_FP16, HPG_FP32,
+                   HPG_FP64, HPG_OK, HpgError,
                    KernelStat, LevelDesc, SolveInfo, StencilParams, check, load)
 
 __all__ = ["setup_problem", "build_mg_hierarchy", "num_levels", "level_info", "permute",
-           "spmv", "mg_vcycle", "gmres_ir_solve", "destroy", "set_profiling",
+           "spmv", "mg_vcycle", "gmres_ir_solve", "destroy", "set_profiling", "set_execution",
            "profile_report", "Problem", "HpgError",
            "HPG_FP64", "HPG_FP32", "HPG_BF16", "HPG_FP16", "load"]
 
@@ -132,6 +133,11 @@ def gmres_ir_solve(h, b, x, tol=1e-9, restart=30, maxit=10000, inner=HPG_FP32, b
 def set_profiling(h, enable=True):
     """hpg_set_profiling: per-kernel-class CUDA-event timing on/off."""
     check(load().hpg_set_profiling(h, 1 if enable else 0), "hpg_set_profiling")
+
+
+def set_execution(h, mode):
+    """hpg_set_execution: HPG_EXEC_GRAPH (default) or HPG_EXEC_EAGER."""
+    check(load().hpg_set_execution(h, mode), "hpg_set_execution")
 
 
 def profile_report(h):

@@ -21,6 +21,7 @@ HPG_ERR_STATE = -7
 HPG_ERR_UNSUPPORTED = -8
 
 HPG_FP64, HPG_FP32, HPG_BF16, HPG_FP16 = 0, 1, 2, 3
+HPG_EXEC_GRAPH, HPG_EXEC_EAGER = 0, 1
 
 
 class StencilParams(ctypes.Structure):
@@ -64,6 +65,7 @@ SIGNATURES = {
     "hpg_mg_vcycle": (_I, [_P, _I, _I, _P, _P, _P]),
     "hpg_gmres_ir_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(SolveInfo), _P]),
     "hpg_set_profiling": (_I, [_P, _I]),
+    "hpg_set_execution": (_I, [_P, _I]),
     "hpg_profile_report": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "hpg_destroy": (_I, [_P]),
     "hpg_status_string": (ctypes.c_char_p, [_I]),

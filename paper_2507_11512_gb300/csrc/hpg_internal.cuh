@@ -152,6 +152,7 @@ struct hpg_problem {
   hpg::Profiler* prof = nullptr;
   long long launches = 0;   // kernel launches enqueued (diagnostics)
   bool profiling = false;   // event-bracketed launches, no PDL
+  bool eager = false;       // host-driven solve instead of the solve graph
   bool pdl_enabled = true;  // programmatic dependent launch on the chain
   bool pdl_next = false;    // the previous stream operation was a kernel
 };

@@ -851,7 +851,7 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
   int status = HPG_OK;
   bool converged = false;
   int graph_launches = 0;
-  const bool use_graph = !h->profiling;
+  const bool use_graph = !h->profiling && !h->eager;
   if (!(rho0 == rho0) || isinf(rho0)) {
     status = HPG_ERR_NAN;
     *ws->st_host = init;
@@ -878,8 +878,8 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
         if ((rc = enqueue_cycle_start<T>(h, nullptr, 0, s))) return rc;
         for (int k = 0; k < m; ++k) {
           if (h->profiling) {
+            // instrumentation only: not counted with the solve's kernels
             HPG_CK(kl(h, delay_kernel, 1, 32, s, 4000000LL));
-            h->launches++;
             h->pdl_next = false;
           }
           if ((rc = enqueue_step<T>(h, k, prec, 0ULL, s))) return rc;
@@ -932,6 +932,15 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
 using namespace hpg;
 
 extern "C" {
+
+HPG_API int hpg_set_execution(hpg_problem_t* h, int mode) {
+  if (!h || (mode != HPG_EXEC_GRAPH && mode != HPG_EXEC_EAGER)) {
+    set_error("hpg_set_execution: invalid handle or mode %d", mode);
+    return HPG_ERR_INVALID;
+  }
+  h->eager = mode == HPG_EXEC_EAGER;
+  return HPG_OK;
+}
 
 HPG_API int hpg_gmres_ir_solve(hpg_problem_t* h, const double* b, double* x, double tol,
                                int restart, int maxit, hpg_prec inner, hpg_prec basis,

@@ -265,6 +265,10 @@ def test_graph_and_eager_paths_agree(inner):
         bt = gpu(b, torch.float64)
         xg = torch.zeros_like(bt)
         ig = hpg.gmres_ir_solve(p.h, bt, xg, tol=1e-10, restart=12, inner=inner)
+        hpg.set_execution(p.h, hpg.HPG_EXEC_EAGER)
+        xq = torch.zeros_like(bt)
+        iq = hpg.gmres_ir_solve(p.h, bt, xq, tol=1e-10, restart=12, inner=inner)
+        hpg.set_execution(p.h, hpg.HPG_EXEC_GRAPH)
         hpg.set_profiling(p.h, True)
         xe = torch.zeros_like(bt)
         ie = hpg.gmres_ir_solve(p.h, bt, xe, tol=1e-10, restart=12, inner=inner)
@@ -274,6 +278,8 @@ def test_graph_and_eager_paths_agree(inner):
     assert ig["iterations"] == ie["iterations"] and ig["restarts"] == ie["restarts"]
     assert ig["kernel_launches"] == ie["kernel_launches"]
     torch.testing.assert_close(xg, xe, rtol=0, atol=0)
+    torch.testing.assert_close(xg, xq, rtol=0, atol=0)
+    assert iq["graph_launches"] == 0 and iq["kernel_launches"] == ig["kernel_launches"]
     names = {r["name"] for r in rep}
     assert {"gs_colour_phase", "spmv", "cgs2_gemvt", "cgs2_reorth", "cgs2_final_norm",
             "arnoldi_finish_givens", "restrict", "prolong", "residual_fp64"} <= names
