@@ -156,6 +156,35 @@ HPG_API int hpg_spmv(hpg_problem_t* h, int level, hpg_prec prec,
 HPG_API int hpg_mg_vcycle(hpg_problem_t* h, int level, hpg_prec prec,
                           const void* r, void* z, void* stream);
 
+/* Allocation-free V-cycle.  The paper has no counterpart: this is an entry
+ * point for callers that cannot allocate device memory when they call --
+ * code running inside a CUDA stream capture (cudaMalloc is not allowed there),
+ * real-time loops that must not stall on the allocator, or memory-pool owners
+ * that forbid allocations outside their pool.  It computes exactly what
+ * hpg_mg_vcycle computes (same kernels, same order, same results), but the
+ * coarse levels' work vectors (restricted residuals and corrections of levels
+ * level+1 .. last) live in one static device array of
+ * HPG_NOALLOC_SCRATCH_BYTES bytes that the library declares at file scope:
+ * every GPU that loads the library holds it until the process exits.
+ * - The caller passes r and z as for hpg_mg_vcycle (device, storage order,
+ *   length n_store of `level`); the handle's hierarchy supplies the matrices.
+ * - Needs 2 * sizeof(prec) * (sum of n_store over the coarse levels) bytes;
+ *   larger requests return HPG_ERR_INVALID with the sizes in hpg_last_error()
+ *   (the coarse levels of the 128^3 grid need 4.8 MB in FP64 and fit; those
+ *   of the 320^3 grid need 37 MB in FP32 and are rejected).
+ * - The call allocates and frees nothing (no cudaMalloc / cudaFree, no
+ *   allocating library routine); it zeroes the part of the array it uses with
+ *   cudaMemsetAsync on `stream`.
+ * - The first call on a device looks up the array's device address once
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ * - All calls share the one array: calls that overlap on the GPU (other
+ *   streams, other threads, other handles) race on it and give wrong results.
+ * Asynchronous on `stream`. */
+#define HPG_NOALLOC_SCRATCH_BYTES (32u << 20)
+HPG_API int hpg_mg_vcycle_noalloc(hpg_problem_t* h, int level, hpg_prec prec,
+                                  const void* r, void* z, void* stream);
+
 /* GMRES-IR (Algorithm 3): restarted right-preconditioned GMRES(restart) with
  * CGS2 and Givens rotations.  The outer residual r = b - A x, its norm, the
  * convergence test ||r||/||b|| < tol, the update x += M^{-1} Q t and the

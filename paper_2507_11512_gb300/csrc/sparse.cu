@@ -307,3 +307,138 @@ HPG_API int hpg_mg_vcycle(hpg_problem_t* h, int level, hpg_prec prec, const void
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ allocation-free V-cycle
+// hpg_mg_vcycle_noalloc: the same V-cycle as hpg_mg_vcycle, but the coarse
+// levels' work vectors (restricted residuals and corrections) live in one
+// file-scope device array instead of buffers the handle allocated.  It is for
+// callers that must not allocate device memory at the time of the call.
+#include <mutex>
+
+namespace hpg {
+
+constexpr size_t kStaticScratchBytes = (size_t)HPG_NOALLOC_SCRATCH_BYTES;
+
+// Shared by every call on a device; every GPU that loads this library holds
+// it until the process exits.
+static __device__ __align__(256) unsigned char g_vcycle_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_scratch_addr[kMaxDevices];
+static std::mutex g_scratch_mutex;
+
+// Device address of g_vcycle_scratch on the current device.  In host code the
+// array's name is only a stand-in, so the address is looked up once per device
+// (with that device current) and cached.
+static int scratch_address(void** out) {
+  int dev = 0;
+  HPG_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("hpg_mg_vcycle_noalloc: device %d out of range", dev);
+    return HPG_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_vcycle_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return HPG_OK;
+}
+
+// Same schedule as vcycle_t; coarse vectors come from crhs / csol.
+template <typename T>
+static int vcycle_noalloc_t(hpg_problem* h, int l, const T* r, T* z, T* const* crhs,
+                            T* const* csol, cudaStream_t s) {
+  const Level& L = h->lev[l];
+  SweepState st;
+  int rc;
+  if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
+  if (h->pre == 0) {
+    HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
+    h->pdl_next = false;
+  }
+  for (int it = 0; it < h->pre; ++it)
+    if ((rc = symgs<T>(h, l, r, z, it == 0, st, s))) return rc;
+  const Level& C = h->lev[l + 1];
+  T* rc_vec = crhs[l + 1];
+  T* zc_vec = csol[l + 1];
+  const long long cnt = (long long)L.g.cdx[kCoarseColour] * L.g.cdy[kCoarseColour] *
+                        L.g.cdz[kCoarseColour];
+  const int prec = Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32;
+  const T* vals = Prec<T>::vals(L);
+  rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
+              "restrict_kernel", [&] {
+                return kl(h, restrict_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
+                          vals, L.cols, r, z, rc_vec);
+              });
+  if (rc) return rc;
+  if ((rc = vcycle_noalloc_t<T>(h, l + 1, rc_vec, zc_vec, crhs, csol, s))) return rc;
+  rc = launch(h, K_PROLONG, l, prec, cnt * 3.0 * sizeof(T), s, "prolong_kernel", [&] {
+    return kl(h, prolong_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
+              (const T*)zc_vec, z);
+  });
+  if (rc) return rc;
+  st.last = -1;
+  for (int it = 0; it < h->post; ++it)
+    if ((rc = symgs<T>(h, l, r, z, false, st, s))) return rc;
+  return HPG_OK;
+}
+
+template <typename T>
+static int vcycle_noalloc_entry(hpg_problem* h, int level, const T* r, T* z, cudaStream_t s) {
+  // carve the coarse vectors of levels level+1 .. nlev-1 out of the array
+  size_t need = 0;
+  for (int l = level + 1; l < h->nlev; ++l) need += 2 * sizeof(T) * (size_t)h->lev[l].g.n_store;
+  if (need > kStaticScratchBytes) {
+    set_error("hpg_mg_vcycle_noalloc: the coarse levels need %zu bytes of work space, more "
+              "than the %zu-byte static array (use hpg_mg_vcycle)",
+              need, kStaticScratchBytes);
+    return HPG_ERR_INVALID;
+  }
+  void* base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc) return rc;
+  T* crhs[kMaxLevels] = {nullptr};
+  T* csol[kMaxLevels] = {nullptr};
+  size_t off = 0;
+  for (int l = level + 1; l < h->nlev; ++l) {
+    crhs[l] = reinterpret_cast<T*>(static_cast<unsigned char*>(base) + off);
+    off += sizeof(T) * (size_t)h->lev[l].g.n_store;
+    csol[l] = reinterpret_cast<T*>(static_cast<unsigned char*>(base) + off);
+    off += sizeof(T) * (size_t)h->lev[l].g.n_store;
+  }
+  // the array keeps the previous call's contents: zero the part this call
+  // uses (padding entries of the coarse vectors must read as zero)
+  if (need > 0) {
+    HPG_CK(cudaMemsetAsync(base, 0, need, s));
+  }
+  h->pdl_next = false;
+  return vcycle_noalloc_t<T>(h, level, r, z, crhs, csol, s);
+}
+
+}  // namespace hpg
+
+extern "C" {
+
+HPG_API int hpg_mg_vcycle_noalloc(hpg_problem_t* h, int level, hpg_prec prec, const void* r,
+                                  void* z, void* stream) {
+  if (!h || !r || !z || level < 0 || level >= h->nlev ||
+      (prec != HPG_FP64 && prec != HPG_FP32) || r == z) {
+    set_error("hpg_mg_vcycle_noalloc: invalid argument (handle, level %d, prec %d, pointers)",
+              level, (int)prec);
+    return HPG_ERR_INVALID;
+  }
+  if (!h->hierarchy) {
+    set_error("hpg_mg_vcycle_noalloc: call hpg_build_mg_hierarchy first");
+    return HPG_ERR_STATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == HPG_FP64)
+    return vcycle_noalloc_entry<double>(h, level, (const double*)r, (double*)z, s);
+  return vcycle_noalloc_entry<float>(h, level, (const float*)r, (float*)z, s);
+}
+
+}  // extern "C"
