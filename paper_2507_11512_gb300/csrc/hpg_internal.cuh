@@ -134,7 +134,7 @@ struct Profiler;    // per-kernel-class CUDA-event timing (profile.cu)
 enum KernelClass {
   K_GEN = 0, K_PERMUTE, K_SPMV, K_RESIDUAL, K_GS, K_RESTRICT, K_PROLONG, K_CGS2_GEMVT,
   K_CGS2_REORTH, K_CGS2_FINAL, K_ARNOLDI_FINISH, K_TRSM, K_COMBINE, K_UPDATE_X,
-  K_CYCLE_START, K_NORM, K_NUM_CLASSES
+  K_CYCLE_START, K_NORM, K_VCYCLE, K_NUM_CLASSES
 };
 const char* kernel_class_name(int cls);
 
@@ -155,6 +155,10 @@ struct hpg_problem {
   bool eager = false;       // host-driven solve instead of the solve graph
   bool pdl_enabled = true;  // programmatic dependent launch on the chain
   bool pdl_next = false;    // the previous stream operation was a kernel
+  bool vcycle_persistent = true;  // one cooperative kernel per V-cycle
+  int pvc_ctas = 0;         // grid of the persistent V-cycle (0: not probed, <0: unusable)
+  unsigned* pvc_bar = nullptr;    // grid-barrier words of the persistent V-cycle
+  int* dev_status = nullptr;      // device-side error word (bounded waits that gave up)
 };
 
 namespace hpg {
@@ -214,6 +218,10 @@ int launch_spmv(hpg_problem* h, int level, hpg_prec prec, const void* x, void* y
 int launch_residual64(hpg_problem* h, const double* b, const double* x, double* r,
                       cudaStream_t s);
 int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
+               cudaStream_t s);
+// Persistent cooperative V-cycle; HPG_ERR_UNSUPPORTED when it cannot run (the
+// caller then uses the one-launch-per-phase V-cycle).
+int launch_pvc(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
                cudaStream_t s);
 int launch_permute(hpg_problem* h, int level, int direction, hpg_prec in_prec,
                    const void* in, hpg_prec out_prec, void* out, cudaStream_t s);

@@ -268,6 +268,10 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
 
 int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
                cudaStream_t s) {
+  if (h->vcycle_persistent) {
+    const int rc = launch_pvc(h, level, prec, r, z, s);
+    if (rc != HPG_ERR_UNSUPPORTED) return rc;
+  }
   if (prec == HPG_FP64) return vcycle_t<double>(h, level, (const double*)r, (double*)z, s);
   return vcycle_t<float>(h, level, (const float*)r, (float*)z, s);
 }

@@ -303,3 +303,57 @@ def test_repeated_solves_recapture():
             res.append(x.cpu().numpy())
         np.testing.assert_array_equal(res[0], res[3])
         np.testing.assert_array_equal(res[3], res[4])
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16), (24, 20, 28), (40, 36, 28), (64, 64, 64),
+                                  (33, 17, 9)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_persistent_vcycle_equals_phase_launches(dims, dtype):
+    # one cooperative kernel per V-cycle vs one launch per phase: same phases,
+    # same arithmetic, so the results are equal
+    with hpg.Problem(*dims, beta=0.5) as p:
+        for l in range(p.levels):
+            info = p.info[l]
+            r = random_vector(info["n"], seed=7 + l,
+                              dtype=np.float64 if dtype == torch.float64 else np.float32)
+            rt = torch.tensor(to_storage(r, info["dims"]), dtype=dtype, device=DEV)
+            hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 1)
+            z1 = p.vcycle(rt, l)
+            hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 0)
+            z2 = p.vcycle(rt, l)
+            hpg.device_status(p.h)
+            np.testing.assert_array_equal(z1.cpu().numpy(), z2.cpu().numpy())
+
+
+def test_persistent_vcycle_sweep_variants():
+    dims = (32, 32, 32)
+    for pre, post in [(0, 1), (2, 2), (1, 3)]:
+        with hpg.Problem(*dims, beta=0.5, pre_sweeps=pre, post_sweeps=post) as p:
+            r = torch.tensor(to_storage(random_vector(32 ** 3, seed=2), dims), device=DEV)
+            z1 = p.vcycle(r)
+            hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 0)
+            z2 = p.vcycle(r)
+            hpg.device_status(p.h)
+            np.testing.assert_array_equal(z1.cpu().numpy(), z2.cpu().numpy())
+
+
+@pytest.mark.parametrize("inner", [hpg.HPG_FP32, hpg.HPG_FP64])
+def test_solve_same_with_and_without_persistent_vcycle(inner):
+    dims, beta = (48, 40, 32), 0.5
+    lv = oracle_hierarchy(dims, 4, beta)
+    b = lv[0].A @ x_true(lv[0].n) + rhs_noise(lv[0].n, 1e-3)
+    with hpg.Problem(*dims, beta=beta) as p:
+        bt = gpu(b, torch.float64)
+        x1 = torch.zeros_like(bt)
+        i1 = hpg.gmres_ir_solve(p.h, bt, x1, inner=inner)
+        hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 0)
+        x2 = torch.zeros_like(bt)
+        i2 = hpg.gmres_ir_solve(p.h, bt, x2, inner=inner)
+        hpg.set_option(p.h, hpg.HPG_OPT_PDL, 0)
+        x3 = torch.zeros_like(bt)
+        i3 = hpg.gmres_ir_solve(p.h, bt, x3, inner=inner)
+    assert i1["iterations"] == i2["iterations"] == i3["iterations"]
+    np.testing.assert_array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    np.testing.assert_array_equal(x2.cpu().numpy(), x3.cpu().numpy())
+    r = np.linalg.norm(b - lv[0].A @ x1.cpu().numpy()) / np.linalg.norm(b)
+    assert r < 1e-9
