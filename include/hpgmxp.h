@@ -56,7 +56,6 @@ extern "C" {
 #define HPG_ERR_ALLOC          -6  /* device allocation failed                    */
 #define HPG_ERR_STATE          -7  /* call out of order (e.g. no hierarchy yet)   */
 #define HPG_ERR_UNSUPPORTED    -8  /* option not built into this library          */
-#define HPG_ERR_TIMEOUT        -9  /* a device-side wait ran out of its limit     */
 
 /* -------------------------------------------------------------- precisions */
 typedef enum {
@@ -242,21 +241,16 @@ HPG_API int hpg_profile_report(hpg_problem_t* h, hpg_kernel_stat* out, int capac
 HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
 
 /* Implementation options (not steps of the method; results are the same).
- * HPG_OPT_VCYCLE_PERSISTENT (default 1): run each V-cycle as one persistent
- * cooperative kernel (one CTA per SM, bounded grid barriers between the
- * colour phases, coarse levels on a 16-CTA subset); 0: one kernel launch per
- * colour phase / transfer.  HPG_OPT_PDL (default 1): programmatic dependent
- * launch between the solve's kernels.  Setting an option drops captured
- * solve graphs.  HPG_ERR_INVALID for an unknown option. */
-#define HPG_OPT_VCYCLE_PERSISTENT 1
+ * HPG_OPT_COARSE_CLUSTER (default 0): run the part of a V-cycle from the
+ * first level with at most 300000 storage rows down to the coarsest (and back)
+ * as one kernel on one thread-block cluster (up to 16 CTAs, hardware cluster
+ * barrier between colour phases); 0: one kernel launch per colour phase /
+ * transfer on every level.  HPG_OPT_PDL (default 1): programmatic dependent
+ * launch between the solve's kernels.  Setting an option drops captured solve
+ * graphs.  HPG_ERR_INVALID for an unknown option. */
+#define HPG_OPT_COARSE_CLUSTER 1
 #define HPG_OPT_PDL 2
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);
-
-/* Waits for the device and reports HPG_ERR_TIMEOUT if a bounded device-side
- * wait (the persistent V-cycle's grid barrier) gave up since the last check,
- * clearing that state; HPG_OK otherwise.  hpg_gmres_ir_solve checks this
- * itself; hpg_mg_vcycle is asynchronous and reports through this call. */
-HPG_API int hpg_device_status(hpg_problem_t* h);
 
 /* Frees everything the handle owns (NULL is accepted). */
 HPG_API int hpg_destroy(hpg_problem_t* h);

@@ -11,14 +11,13 @@ import ctypes
 
 from ._lib import (HPG_BF16, HPG_ERR_ALLOC, HPG_ERR_BREAKDOWN, HPG_ERR_CUDA,  # noqa: F401
                    HPG_ERR_INVALID, HPG_ERR_NAN, HPG_ERR_NOT_CONVERGED, HPG_ERR_STATE,
-                   HPG_ERR_TIMEOUT, HPG_ERR_UNSUPPORTED, HPG_EXEC_EAGER, HPG_EXEC_GRAPH,
-                   HPG_FP16, HPG_FP32, HPG_FP64, HPG_OK, HPG_OPT_PDL,
-                   HPG_OPT_VCYCLE_PERSISTENT, HpgError,
+                   HPG_ERR_UNSUPPORTED, HPG_EXEC_EAGER, HPG_EXEC_GRAPH, HPG_FP16, HPG_FP32,
+                   HPG_FP64, HPG_OK, HPG_OPT_COARSE_CLUSTER, HPG_OPT_PDL, HpgError,
                    KernelStat, LevelDesc, SolveInfo, StencilParams, check, load)
 
 __all__ = ["setup_problem", "build_mg_hierarchy", "num_levels", "level_info", "permute",
            "spmv", "mg_vcycle", "gmres_ir_solve", "destroy", "set_profiling", "set_execution",
-           "set_option", "device_status",
+           "set_option",
            "profile_report", "Problem", "HpgError",
            "HPG_FP64", "HPG_FP32", "HPG_BF16", "HPG_FP16", "load"]
 
@@ -143,14 +142,8 @@ def set_execution(h, mode):
 
 
 def set_option(h, option, value):
-    """hpg_set_option: HPG_OPT_VCYCLE_PERSISTENT or HPG_OPT_PDL, 0 / 1."""
+    """hpg_set_option: HPG_OPT_COARSE_CLUSTER or HPG_OPT_PDL, 0 / 1."""
     check(load().hpg_set_option(h, option, int(value)), "hpg_set_option")
-
-
-def device_status(h):
-    """hpg_device_status: raises HpgError(HPG_ERR_TIMEOUT) if a bounded device
-    wait gave up since the last check."""
-    check(load().hpg_device_status(h), "hpg_device_status")
 
 
 def profile_report(h):

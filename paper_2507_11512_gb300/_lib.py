@@ -19,11 +19,10 @@ HPG_ERR_NAN = -5
 HPG_ERR_ALLOC = -6
 HPG_ERR_STATE = -7
 HPG_ERR_UNSUPPORTED = -8
-HPG_ERR_TIMEOUT = -9
 
 HPG_FP64, HPG_FP32, HPG_BF16, HPG_FP16 = 0, 1, 2, 3
 HPG_EXEC_GRAPH, HPG_EXEC_EAGER = 0, 1
-HPG_OPT_VCYCLE_PERSISTENT, HPG_OPT_PDL = 1, 2
+HPG_OPT_COARSE_CLUSTER, HPG_OPT_PDL = 1, 2
 
 
 class StencilParams(ctypes.Structure):
@@ -70,7 +69,6 @@ SIGNATURES = {
     "hpg_set_profiling": (_I, [_P, _I]),
     "hpg_set_execution": (_I, [_P, _I]),
     "hpg_set_option": (_I, [_P, _I, _I]),
-    "hpg_device_status": (_I, [_P]),
     "hpg_profile_report": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "hpg_destroy": (_I, [_P]),
     "hpg_status_string": (ctypes.c_char_p, [_I]),

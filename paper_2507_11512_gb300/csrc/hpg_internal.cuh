@@ -77,6 +77,18 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
 
+// Matrix load of a level: streamed (evict-first) on levels larger than L2,
+// cached normally on coarse levels, which every sweep reads again.
+template <bool STREAM, typename V>
+__device__ __forceinline__ V ld_matrix(const V* p) {
+  if (STREAM) return __ldcs(p);
+  return __ldg(p);
+}
+
+// Levels whose FP32 ELL slots exceed this many bytes stream their matrix
+// (evict-first); smaller (coarse) levels keep theirs in the 126 MB L2.
+constexpr long long kStreamMatrixBytes = 96LL << 20;
+
 // ---------------------------------------------- programmatic dependent launch
 // Kernels of the solve chain are launched with programmatic stream
 // serialization: the next kernel may start while its predecessor drains.
@@ -155,10 +167,8 @@ struct hpg_problem {
   bool eager = false;       // host-driven solve instead of the solve graph
   bool pdl_enabled = true;  // programmatic dependent launch on the chain
   bool pdl_next = false;    // the previous stream operation was a kernel
-  bool vcycle_persistent = true;  // one cooperative kernel per V-cycle
-  int pvc_ctas = 0;         // grid of the persistent V-cycle (0: not probed, <0: unusable)
-  unsigned* pvc_bar = nullptr;    // grid-barrier words of the persistent V-cycle
-  int* dev_status = nullptr;      // device-side error word (bounded waits that gave up)
+  bool coarse_cluster = false;    // coarse levels of a V-cycle in one cluster kernel
+  int vc_cluster[2] = {0, 0};     // its cluster size per precision (0: not probed, <0: none)
 };
 
 namespace hpg {
@@ -219,10 +229,11 @@ int launch_residual64(hpg_problem* h, const double* b, const double* x, double* 
                       cudaStream_t s);
 int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
                cudaStream_t s);
-// Persistent cooperative V-cycle; HPG_ERR_UNSUPPORTED when it cannot run (the
-// caller then uses the one-launch-per-phase V-cycle).
-int launch_pvc(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
-               cudaStream_t s);
+// V-cycle from `level` down in one thread-block cluster; HPG_ERR_UNSUPPORTED
+// when the level is too large or no cluster fits (the caller then launches
+// one kernel per phase).
+int launch_vcycle_cluster(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
+                          cudaStream_t s);
 int launch_permute(hpg_problem* h, int level, int direction, hpg_prec in_prec,
                    const void* in, hpg_prec out_prec, void* out, cudaStream_t s);
 void destroy_workspace(hpg_problem* h);

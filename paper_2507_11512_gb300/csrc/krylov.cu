@@ -514,7 +514,7 @@ norm2_kernel(const double* __restrict__ v, long long ns, double* __restrict__ pa
 // ||r|| / ||b|| < tol ends the solve; so do a recorded breakdown / NaN and
 // maxit.  In graph mode it sets the WHILE node's condition.
 __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* st,
-                                   const int* __restrict__ dev_status, unsigned long long loop) {
+                                   unsigned long long loop) {
   pdl_trigger();
   pdl_wait();
   if (threadIdx.x != 0) return;
@@ -523,9 +523,7 @@ __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* 
   st->rho = rho;
   st->rel = rel;
   bool done = true;
-  if (*dev_status != 0) {
-    st->status = HPG_ERR_TIMEOUT;   // a persistent kernel's bounded wait gave up
-  } else if (!isfinite(rel)) {
+  if (!isfinite(rel)) {
     st->status = HPG_ERR_NAN;
   } else if (rel < st->tol) {
     st->converged = 1;
@@ -665,8 +663,7 @@ static int enqueue_outer(hpg_problem* h, unsigned long long loop, cudaStream_t s
                   });
   if (rc) return rc;
   return launch(h, K_NORM, 0, HPG_FP64, 0.0, s, "outer_check_kernel", [&] {
-    return kl(h, outer_check_kernel, 1, 32, s, (const double*)ws->rho2, ws->st,
-              (const int*)h->dev_status, loop);
+    return kl(h, outer_check_kernel, 1, 32, s, (const double*)ws->rho2, ws->st, loop);
   });
 }
 
@@ -906,11 +903,6 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
   HPG_CK(cudaStreamSynchronize(s));
   h->pdl_next = false;
   const SolveState& fs = *ws->st_host;
-  if (fs.status == HPG_ERR_TIMEOUT || status == HPG_ERR_TIMEOUT) {
-    hpg_device_status(h);   // clears the device word and the barrier state
-    status = HPG_ERR_TIMEOUT;
-    converged = false;
-  }
   if (info) {
     info->iterations = fs.iters;
     info->restarts = fs.restarts;

@@ -273,7 +273,6 @@ HPG_API const char* hpg_status_string(int status) {
     case HPG_ERR_ALLOC: return "HPG_ERR_ALLOC";
     case HPG_ERR_STATE: return "HPG_ERR_STATE";
     case HPG_ERR_UNSUPPORTED: return "HPG_ERR_UNSUPPORTED";
-    case HPG_ERR_TIMEOUT: return "HPG_ERR_TIMEOUT";
   }
   return "HPG_ERR_UNKNOWN";
 }
@@ -392,8 +391,6 @@ HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels, int pre_sweeps,
       if (rc == HPG_OK) rc = dev_alloc(&L.sol[pi], es * L.g.n_store);
     }
   }
-  if (rc == HPG_OK && !h->pvc_bar) rc = dev_alloc((void**)&h->pvc_bar, 128 * sizeof(unsigned));
-  if (rc == HPG_OK && !h->dev_status) rc = dev_alloc((void**)&h->dev_status, 16);
   if (rc == HPG_OK) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = cuda_fail(e, "hierarchy build", __FILE__, __LINE__);
@@ -444,30 +441,13 @@ HPG_API int hpg_permute(hpg_problem_t* h, int level, int direction, hpg_prec in_
   return launch_permute(h, level, direction, in_prec, in, out_prec, out, (cudaStream_t)stream);
 }
 
-HPG_API int hpg_device_status(hpg_problem_t* h) {
-  if (!h) {
-    set_error("hpg_device_status: NULL handle");
-    return HPG_ERR_INVALID;
-  }
-  HPG_CK(cudaDeviceSynchronize());
-  if (!h->dev_status) return HPG_OK;
-  int st = 0;
-  HPG_CK(cudaMemcpy(&st, h->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (st == 0) return HPG_OK;
-  // a bounded device wait gave up: clear the word and the barrier state
-  HPG_CK(cudaMemset(h->dev_status, 0, 16));
-  if (h->pvc_bar) HPG_CK(cudaMemset(h->pvc_bar, 0, 128 * sizeof(unsigned)));
-  set_error("a device-side wait ran out of its iteration limit");
-  return HPG_ERR_TIMEOUT;
-}
-
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
   if (!h) {
     set_error("hpg_set_option: NULL handle");
     return HPG_ERR_INVALID;
   }
   switch (option) {
-    case HPG_OPT_VCYCLE_PERSISTENT: h->vcycle_persistent = value != 0; break;
+    case HPG_OPT_COARSE_CLUSTER: h->coarse_cluster = value != 0; break;
     case HPG_OPT_PDL: h->pdl_enabled = value != 0; break;
     default:
       set_error("hpg_set_option: unknown option %d", option);
@@ -482,8 +462,6 @@ HPG_API int hpg_destroy(hpg_problem_t* h) {
   destroy_workspace(h);
   destroy_profiler(h);
   for (int l = 0; l < kMaxLevels; ++l) free_level(h->lev[l], false);
-  dev_free(h->pvc_bar);
-  dev_free(h->dev_status);
   delete h;
   return HPG_OK;
 }

@@ -71,8 +71,10 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
 // launch.  Entries x_j with j >= valid_end read as zero: the first forward
 // sweep from z = 0 passes valid_end = start of the current colour block, so
 // that colours not yet visited count as zero without a memset.
-template <typename T>
-__global__ void __launch_bounds__(256)
+// 32 registers at most: eight 256-thread CTAs per SM, so the 1024 CTAs of a
+// 128^3 colour phase are resident in a single wave.
+template <typename T, bool STREAM>
+__global__ void __launch_bounds__(256, 8)
 gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                 const T* __restrict__ r, T* x, long long row0, long long nrows,
                 long long valid_end) {
@@ -87,12 +89,12 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     if (s == kCentre) continue;
-    const T a = ld_stream(vals + s * ns + row);
-    const int c = ld_stream(cols + s * ns + row);
+    const T a = ld_matrix<STREAM>(vals + s * ns + row);
+    const int c = ld_matrix<STREAM>(cols + s * ns + row);
     const T xv = (c < valid_end) ? __ldg(x + c) : T(0);
     acc = fma(-a, xv, acc);
   }
-  const T diag = ld_stream(vals + kCentre * ns + row);
+  const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
   x[row] = acc / diag;
 }
 
@@ -101,7 +103,7 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
 // coarse-coincident fine points are exactly fine colour block 7, stored in the
 // same lexicographic order as the coarse grid, so threads walk that block
 // contiguously and scatter into the coarse colour blocks.
-template <typename T>
+template <typename T, bool STREAM>
 __global__ void __launch_bounds__(256)
 restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                 const T* __restrict__ vals, const int* __restrict__ cols,
@@ -122,8 +124,8 @@ restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc
   T acc = r[row];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
-    const T a = ld_stream(vals + s * ns + row);
-    const int c = ld_stream(cols + s * ns + row);
+    const T a = ld_matrix<STREAM>(vals + s * ns + row);
+    const int c = ld_matrix<STREAM>(cols + s * ns + row);
     acc = fma(-a, __ldg(z + c), acc);
   }
   const int I = (int)(p % cx);
@@ -212,8 +214,10 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
   const T* vals = Prec<T>::vals(L);
   return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32,
                 L.cnt[c] * bytes_gs_row(sizeof(T), sizeof(T)), s, "gs_phase_kernel", [&] {
-                  return kl(h, gs_phase_kernel<T>, grid_for(nrows, kThreads), kThreads, s, vals,
-                            L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                  const bool stream = L.g.n_store * 27LL * 8 > kStreamMatrixBytes;
+                  return kl(h, stream ? gs_phase_kernel<T, true> : gs_phase_kernel<T, false>,
+                            grid_for(nrows, kThreads), kThreads, s, vals, L.cols, L.g.n_store, r,
+                            z, row0, nrows, valid_end);
                 });
 }
 
@@ -233,7 +237,8 @@ template <typename T>
 static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   const Level& L = h->lev[l];
   SweepState st;
-  int rc;
+  int rc = launch_vcycle_cluster(h, l, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32, r, z, s);
+  if (rc != HPG_ERR_UNSUPPORTED) return rc;   // small level: the rest runs in one cluster
   if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
   if (h->pre == 0) {
     HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
@@ -250,8 +255,10 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   const T* vals = Prec<T>::vals(L);
   rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
               "restrict_kernel", [&] {
-                return kl(h, restrict_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
-                          vals, L.cols, r, z, rc_vec);
+                const bool stream = L.g.n_store * 27LL * 8 > kStreamMatrixBytes;
+                return kl(h, stream ? restrict_kernel<T, true> : restrict_kernel<T, false>,
+                          grid_for(cnt, kThreads), kThreads, s, L.g, C.g, vals, L.cols, r, z,
+                          rc_vec);
               });
   if (rc) return rc;
   if ((rc = vcycle_t<T>(h, l + 1, rc_vec, zc_vec, s))) return rc;
@@ -268,10 +275,6 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
 
 int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
                cudaStream_t s) {
-  if (h->vcycle_persistent) {
-    const int rc = launch_pvc(h, level, prec, r, z, s);
-    if (rc != HPG_ERR_UNSUPPORTED) return rc;
-  }
   if (prec == HPG_FP64) return vcycle_t<double>(h, level, (const double*)r, (double*)z, s);
   return vcycle_t<float>(h, level, (const float*)r, (float*)z, s);
 }
@@ -375,8 +378,10 @@ static int vcycle_noalloc_t(hpg_problem* h, int l, const T* r, T* z, T* const* c
   const T* vals = Prec<T>::vals(L);
   rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
               "restrict_kernel", [&] {
-                return kl(h, restrict_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
-                          vals, L.cols, r, z, rc_vec);
+                const bool stream = L.g.n_store * 27LL * 8 > kStreamMatrixBytes;
+                return kl(h, stream ? restrict_kernel<T, true> : restrict_kernel<T, false>,
+                          grid_for(cnt, kThreads), kThreads, s, L.g, C.g, vals, L.cols, r, z,
+                          rc_vec);
               });
   if (rc) return rc;
   if ((rc = vcycle_noalloc_t<T>(h, l + 1, rc_vec, zc_vec, crhs, csol, s))) return rc;

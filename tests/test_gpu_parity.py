@@ -281,10 +281,28 @@ def test_graph_and_eager_paths_agree(inner):
     torch.testing.assert_close(xg, xq, rtol=0, atol=0)
     assert iq["graph_launches"] == 0 and iq["kernel_launches"] == ig["kernel_launches"]
     names = {r["name"] for r in rep}
-    assert {"gs_colour_phase", "spmv", "cgs2_gemvt", "cgs2_reorth", "cgs2_final_norm",
-            "arnoldi_finish_givens", "restrict", "prolong", "residual_fp64"} <= names
+    assert {"gs_colour_phase", "restrict", "prolong", "spmv", "cgs2_gemvt", "cgs2_reorth",
+            "cgs2_final_norm", "arnoldi_finish_givens", "residual_fp64"} <= names
+    # with the coarse-level cluster kernel the whole (small) V-cycle is one kernel
+    with hpg.Problem(*dims, beta=beta) as p:
+        hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 1)
+        hpg.set_profiling(p.h, True)
+        xc = torch.zeros_like(bt)
+        ic = hpg.gmres_ir_solve(p.h, bt, xc, tol=1e-10, restart=12, inner=inner)
+        repc = hpg.profile_report(p.h)
+    torch.testing.assert_close(xg, xc, rtol=0, atol=0)
+    vc = [r for r in repc if r["name"] == "vcycle_coarse_cluster"][0]
+    assert vc["launches"] == ic["iterations"] + ic["restarts"]
+    with hpg.Problem(*dims, beta=beta) as p:
+        hpg.set_profiling(p.h, True)
+        xp = torch.zeros_like(bt)
+        ip = hpg.gmres_ir_solve(p.h, bt, xp, tol=1e-10, restart=12, inner=inner)
+        rep = hpg.profile_report(p.h)
+    torch.testing.assert_close(xg, xp, rtol=0, atol=0)
+    names = {r["name"] for r in rep}
+    assert {"gs_colour_phase", "restrict", "prolong"} <= names
     gs0 = [r for r in rep if r["name"] == "gs_colour_phase" and r["level"] == 0][0]
-    assert gs0["launches"] == (ie["iterations"] + ie["restarts"]) * 30
+    assert gs0["launches"] == (ip["iterations"] + ip["restarts"]) * 30
     assert gs0["total_ms"] > 0 and gs0["bytes"] > 0
 
 
@@ -308,45 +326,45 @@ def test_repeated_solves_recapture():
 @pytest.mark.parametrize("dims", [(16, 16, 16), (24, 20, 28), (40, 36, 28), (64, 64, 64),
                                   (33, 17, 9)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_persistent_vcycle_equals_phase_launches(dims, dtype):
-    # one cooperative kernel per V-cycle vs one launch per phase: same phases,
-    # same arithmetic, so the results are equal
+def test_cluster_vcycle_equals_phase_launches(dims, dtype):
+    # coarse levels in one cluster kernel vs one launch per phase: same
+    # phases, same arithmetic, so the results are equal
     with hpg.Problem(*dims, beta=0.5) as p:
         for l in range(p.levels):
             info = p.info[l]
             r = random_vector(info["n"], seed=7 + l,
                               dtype=np.float64 if dtype == torch.float64 else np.float32)
             rt = torch.tensor(to_storage(r, info["dims"]), dtype=dtype, device=DEV)
-            hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 1)
+            hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 1)
             z1 = p.vcycle(rt, l)
-            hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 0)
+            hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 0)
             z2 = p.vcycle(rt, l)
-            hpg.device_status(p.h)
             np.testing.assert_array_equal(z1.cpu().numpy(), z2.cpu().numpy())
 
 
-def test_persistent_vcycle_sweep_variants():
+def test_cluster_vcycle_sweep_variants():
     dims = (32, 32, 32)
     for pre, post in [(0, 1), (2, 2), (1, 3)]:
         with hpg.Problem(*dims, beta=0.5, pre_sweeps=pre, post_sweeps=post) as p:
             r = torch.tensor(to_storage(random_vector(32 ** 3, seed=2), dims), device=DEV)
+            hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 1)
             z1 = p.vcycle(r)
-            hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 0)
+            hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 0)
             z2 = p.vcycle(r)
-            hpg.device_status(p.h)
             np.testing.assert_array_equal(z1.cpu().numpy(), z2.cpu().numpy())
 
 
 @pytest.mark.parametrize("inner", [hpg.HPG_FP32, hpg.HPG_FP64])
-def test_solve_same_with_and_without_persistent_vcycle(inner):
+def test_solve_same_with_and_without_cluster_vcycle(inner):
     dims, beta = (48, 40, 32), 0.5
     lv = oracle_hierarchy(dims, 4, beta)
     b = lv[0].A @ x_true(lv[0].n) + rhs_noise(lv[0].n, 1e-3)
     with hpg.Problem(*dims, beta=beta) as p:
         bt = gpu(b, torch.float64)
+        hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 1)
         x1 = torch.zeros_like(bt)
         i1 = hpg.gmres_ir_solve(p.h, bt, x1, inner=inner)
-        hpg.set_option(p.h, hpg.HPG_OPT_VCYCLE_PERSISTENT, 0)
+        hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 0)
         x2 = torch.zeros_like(bt)
         i2 = hpg.gmres_ir_solve(p.h, bt, x2, inner=inner)
         hpg.set_option(p.h, hpg.HPG_OPT_PDL, 0)
