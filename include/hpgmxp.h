@@ -56,6 +56,7 @@ extern "C" {
 #define HPG_ERR_ALLOC          -6  /* device allocation failed                    */
 #define HPG_ERR_STATE          -7  /* call out of order (e.g. no hierarchy yet)   */
 #define HPG_ERR_UNSUPPORTED    -8  /* option not built into this library          */
+#define HPG_ERR_TIMEOUT        -9  /* a device-side wait ran out of its limit     */
 
 /* -------------------------------------------------------------- precisions */
 typedef enum {

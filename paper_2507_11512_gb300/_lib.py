@@ -19,6 +19,7 @@ HPG_ERR_NAN = -5
 HPG_ERR_ALLOC = -6
 HPG_ERR_STATE = -7
 HPG_ERR_UNSUPPORTED = -8
+HPG_ERR_TIMEOUT = -9
 
 HPG_FP64, HPG_FP32, HPG_BF16, HPG_FP16 = 0, 1, 2, 3
 HPG_EXEC_GRAPH, HPG_EXEC_EAGER = 0, 1

@@ -64,6 +64,7 @@ struct Workspace {
   double* t = nullptr;
   double* y = nullptr;
   double* rho2 = nullptr;  // ||r||^2 of the outer residual
+  int* dev_err = nullptr;  // set by a kernel whose bounded wait gave up
   SolveState* st = nullptr;      // device
   SolveState* st_host = nullptr; // pinned mirror
   unsigned long long* hk = nullptr;  // [m] IF-node handles of the captured cycle
@@ -87,7 +88,7 @@ void destroy_workspace(hpg_problem* h) {
     if (ws->cap[i]) cudaStreamDestroy(ws->cap[i]);
   void* ptrs[] = {ws->Q,  ws->z,  ws->w,  ws->u,  ws->b,  ws->x,    ws->r,
                   ws->stage, ws->partials, ws->counter, ws->h1, ws->h2, ws->H, ws->cs,
-                  ws->sn, ws->t,  ws->y,  ws->rho2, ws->st, ws->hk};
+                  ws->sn, ws->t,  ws->y,  ws->rho2, ws->st, ws->hk, ws->dev_err};
   for (void* p : ptrs) dev_free(p);
   if (ws->st_host) cudaFreeHost(ws->st_host);
   delete ws;
@@ -104,10 +105,10 @@ static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec) {
   const size_t es = prec_size(prec);
   ws->m = m;
   ws->prec = prec;
-  // reduction grids: one 1024-row tile per CTA up to 4 CTAs per SM, in whole
-  // clusters
-  long long g = (ns + 4 * kRedThreads - 1) / (4 * kRedThreads);
-  const long long gmax = 4LL * h->num_sms;
+  // reduction grids: up to 8 CTAs per SM, in whole clusters (the TMA passes
+  // use as many resident clusters as fit, at most G)
+  long long g = (ns + kRedThreads - 1) / kRedThreads;
+  const long long gmax = 8LL * h->num_sms;
   if (g > gmax) g = gmax;
   g = (g + kCluster - 1) / kCluster * kCluster;
   ws->G = (int)(g < kCluster ? kCluster : g);
@@ -131,6 +132,7 @@ static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec) {
   rc = rc ? rc : dev_alloc((void**)&ws->y, 8 * (m + 1));
   rc = rc ? rc : dev_alloc((void**)&ws->st, sizeof(SolveState));
   rc = rc ? rc : dev_alloc((void**)&ws->rho2, 16);
+  rc = rc ? rc : dev_alloc((void**)&ws->dev_err, 16);
   rc = rc ? rc : dev_alloc((void**)&ws->hk, sizeof(unsigned long long) * (m + 1));
   for (int i = 0; i < 3 && rc == HPG_OK; ++i) {
     cudaError_t e = cudaStreamCreateWithFlags(&ws->cap[i], cudaStreamNonBlocking);
@@ -258,86 +260,121 @@ template <> struct Vec4<double> {
 //   kReorth:  h2 = Q^T (w - Q h1)                            (GEMV + reorth GEMVT)
 //   kFinal:   q_new = (w - Q h1) - Q h2, partial ||q_new||^2  (reorth GEMV + norm)
 // The GEMV w - Q h1 is recomputed row-locally in the last pass (same code,
-// same rounding) instead of being stored.  Each thread owns 4 consecutive
-// rows per grid-stride step and reads every basis column as one 16-byte (or
-// 32-byte) vector, so even a 2-column step keeps enough bytes in flight.
+// same rounding) instead of being stored.
+//
+// Each CTA walks row tiles of TR rows (a multiple of 32).  Thread 0 streams a tile
+// of w and of the k+1 basis columns into shared memory with TMA bulk copies
+// (one per vector, completion counted on an mbarrier), double-buffered, so the
+// next tile is in flight while this one is used; threads then read the tile
+// from shared memory (row r of column j at stage[(j+1)*TR + r]: consecutive
+// threads, consecutive words).  A thread keeps only its k+1 accumulators.
+// The host picks TR so the two stages hold ~48 KB whatever k is.
 enum PassKind { kGemvT = 0, kReorth = 1, kFinal = 2 };
 
 template <typename T, int KMAX, int KIND>
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kRedThreads)
-cgs2_pass_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __restrict__ w,
-                 const double* __restrict__ h1, const double* __restrict__ h2,
-                 T* __restrict__ qnew, double* __restrict__ partials, unsigned int* counter,
-                 double* __restrict__ out) {
-  pdl_trigger();
-  pdl_wait();
+cgs2_tma_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __restrict__ w,
+                const double* __restrict__ h1, const double* __restrict__ h2,
+                T* __restrict__ qnew, int TR, double* __restrict__ partials,
+                unsigned int* counter, double* __restrict__ out, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(8) unsigned long long bar[2];
   __shared__ T sh1[KMAX], sh2[KMAX];
+  __shared__ int s_abort;
+  pdl_trigger();
+  const int tid = threadIdx.x;
+  const long long ntiles = (ns + TR - 1) / TR;
+  T* const stage0 = reinterpret_cast<T*>(tma_smem);
+  T* const stage1 = stage0 + (long long)(ncol + 1) * TR;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  pdl_wait();   // w, Q and h come from earlier kernels
   if (KIND != kGemvT) {
-    for (int j = threadIdx.x; j < ncol; j += kRedThreads) {
+    for (int j = tid; j < ncol; j += kRedThreads) {
       sh1[j] = (T)h1[j];
       if (KIND == kFinal) sh2[j] = (T)h2[j];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  // thread 0: bring tile t into stage s
+  auto issue = [&](long long t, int sidx) {
+    if (t >= ntiles) return;
+    const long long r0 = t * TR;
+    const long long rows = ns - r0 < TR ? ns - r0 : TR;
+    const unsigned bytes = (unsigned)(rows * sizeof(T));
+    T* const dst = sidx ? stage1 : stage0;
+    unsigned long long* const b = sidx ? &bar[1] : &bar[0];
+    mbar_expect_tx(b, bytes * (unsigned)(ncol + 1));
+    bulk_g2s(dst, w + r0, bytes, b);
+    for (int j = 0; j < ncol; ++j) bulk_g2s(dst + (long long)(j + 1) * TR, Q + j * ns + r0, bytes, b);
+  };
+  if (tid == 0) {
+    issue(blockIdx.x, 0);
+    issue(blockIdx.x + gridDim.x, 1);
   }
   T acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = T(0);
-  const long long groups = ns >> 2;
-  const long long stride = (long long)gridDim.x * kRedThreads;
-  for (long long g = blockIdx.x * (long long)kRedThreads + threadIdx.x; g < groups;
-       g += stride) {
-    const long long i = g << 2;
-    T wv[4];
-    Vec4<T>::ld_cs(w + i, wv);
-    if (KIND == kGemvT) {
+  unsigned phase0 = 0u, phase1 = 0u;
+  int sidx = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const bool ok = sidx ? mbar_wait(&bar[1], phase1) : mbar_wait(&bar[0], phase0);
+    if (!ok) s_abort = 1;
+    if (sidx) phase1 ^= 1u; else phase0 ^= 1u;
+    const T* st = sidx ? stage1 : stage0;
+    const int rows = (int)(ns - t * TR < TR ? ns - t * TR : TR);
+    if (ok) {
+      for (int r = tid; r < rows; r += kRedThreads) {
+        T wr = st[r];
+        if (KIND == kGemvT) {
 #pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < ncol) {
-          T q[4];
-          Vec4<T>::ld_cs(Q + j * ns + i, q);
+          for (int j = 0; j < KMAX; ++j)
+            if (j < ncol) acc[j] = fma(st[(j + 1) * TR + r], wr, acc[j]);
+        } else if (KIND == kReorth) {
+          T s1 = T(0);
 #pragma unroll
-          for (int r = 0; r < 4; ++r) acc[j] = fma(q[r], wv[r], acc[j]);
+          for (int j = 0; j < KMAX; ++j)
+            if (j < ncol) s1 = fma(st[(j + 1) * TR + r], sh1[j], s1);
+          wr = wr - s1;   // w - Q h1
+#pragma unroll
+          for (int j = 0; j < KMAX; ++j)
+            if (j < ncol) acc[j] = fma(st[(j + 1) * TR + r], wr, acc[j]);
+        } else {
+          T s1 = T(0), s2 = T(0);
+#pragma unroll
+          for (int j = 0; j < KMAX; ++j)
+            if (j < ncol) {
+              const T q = st[(j + 1) * TR + r];
+              s1 = fma(q, sh1[j], s1);
+              s2 = fma(q, sh2[j], s2);
+            }
+          wr = (wr - s1) - s2;   // (w - Q h1) - Q h2
+          qnew[t * TR + r] = wr;
+          acc[0] = fma(wr, wr, acc[0]);
         }
-    } else if (KIND == kReorth) {
-      T s1[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < ncol) {
-          T q[4];
-          Vec4<T>::ld_cg(Q + j * ns + i, q);
-#pragma unroll
-          for (int r = 0; r < 4; ++r) s1[r] = fma(q[r], sh1[j], s1[r]);
-        }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) wv[r] = wv[r] - s1[r];   // w - Q h1
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < ncol) {
-          T q[4];
-          Vec4<T>::ld_cg(Q + j * ns + i, q);   // second read, from L2
-#pragma unroll
-          for (int r = 0; r < 4; ++r) acc[j] = fma(q[r], wv[r], acc[j]);
-        }
-    } else {
-      T s1[4] = {T(0), T(0), T(0), T(0)}, s2[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < ncol) {
-          T q[4];
-          Vec4<T>::ld_cs(Q + j * ns + i, q);
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            s1[r] = fma(q[r], sh1[j], s1[r]);
-            s2[r] = fma(q[r], sh2[j], s2[r]);
-          }
-        }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        wv[r] = (wv[r] - s1[r]) - s2[r];   // (w - Q h1) - Q h2
-        acc[0] = fma(wv[r], wv[r], acc[0]);
       }
-      Vec4<T>::st(qnew + i, wv);
     }
+    __syncthreads();   // every thread is done with this stage (and s_abort is seen)
+    if (s_abort) break;
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      issue(t + 2LL * gridDim.x, sidx);
+    }
+    sidx ^= 1;
+  }
+  if (s_abort) {
+    // a copy never completed: flag it, give the copies in flight a bounded
+    // chance to land before the CTA's shared memory goes away
+    if (tid == 0) {
+      atomicExch(err, 1);
+      mbar_wait(&bar[0], phase0);
+      mbar_wait(&bar[1], phase1);
+    }
+    __syncthreads();
   }
   reduce_publish<T, KMAX>(acc, KIND == kFinal ? 1 : ncol, partials, counter, out);
 }
@@ -514,7 +551,7 @@ norm2_kernel(const double* __restrict__ v, long long ns, double* __restrict__ pa
 // ||r|| / ||b|| < tol ends the solve; so do a recorded breakdown / NaN and
 // maxit.  In graph mode it sets the WHILE node's condition.
 __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* st,
-                                   unsigned long long loop) {
+                                   const int* __restrict__ dev_err, unsigned long long loop) {
   pdl_trigger();
   pdl_wait();
   if (threadIdx.x != 0) return;
@@ -523,7 +560,9 @@ __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* 
   st->rho = rho;
   st->rel = rel;
   bool done = true;
-  if (!isfinite(rel)) {
+  if (*dev_err != 0) {
+    st->status = HPG_ERR_TIMEOUT;   // a kernel's bounded wait gave up
+  } else if (!isfinite(rel)) {
     st->status = HPG_ERR_NAN;
   } else if (rel < st->tol) {
     st->converged = 1;
@@ -573,27 +612,93 @@ __global__ void delay_kernel(long long cycles) {
 // ----------------------------------------------------------------- launchers
 template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? HPG_FP64 : HPG_FP32; }
 
+// Tile rows: two stages of (w + ncol columns) x TR in the shared memory a
+// CTA may use without opting in (48 KB) minus the kernel's static shared
+// memory; TR a multiple of 32 in [32, 2048] (16-byte aligned copies and
+// sizes).
+template <typename T>
+static int tma_rows(int ncol, size_t static_smem) {
+  const long long per_row = 2LL * (ncol + 1) * sizeof(T);
+  const long long budget = 48LL * 1024 - (long long)static_smem - 256;
+  long long tr = budget / per_row / 32 * 32;
+  if (tr < 32) tr = 32;
+  if (tr > 2048) tr = 2048;
+  return (int)tr;
+}
+
+template <typename T, int KMAX, int KIND>
+static size_t tma_static_smem() {
+  static size_t bytes = 0;
+  if (bytes == 0) {
+    cudaFuncAttributes a;
+    bytes = cudaFuncGetAttributes(&a, cgs2_tma_kernel<T, KMAX, KIND>) == cudaSuccess
+                ? a.sharedSizeBytes
+                : 16384;
+    cudaGetLastError();
+  }
+  return bytes;
+}
+
+// Grid of a TMA pass: as many whole clusters as can be resident at once.
+template <typename T, int KMAX, int KIND>
+static int tma_grid(hpg_problem* h, size_t smem) {
+  auto kern = cgs2_tma_kernel<T, KMAX, KIND>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCluster);
+  cfg.blockDim = dim3(kRedThreads);
+  cfg.dynamicSmemBytes = smem;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    nclusters = h->num_sms / kCluster;
+  }
+  const int cap = h->ws->G;   // partials are sized for this many CTAs
+  int g = nclusters * kCluster;
+  return g < cap ? g : cap;
+}
+
+template <typename T, int KMAX, int KIND>
+static cudaError_t enqueue_tma(hpg_problem* h, const T* Q, long long ns, int ncol, const T* w,
+                               T* qnew, double* out, cudaStream_t s, int* grid_out) {
+  Workspace* ws = h->ws;
+  const size_t ssmem = tma_static_smem<T, KMAX, KIND>();
+  const int tr = tma_rows<T>(ncol, ssmem);
+  const size_t smem = 2 * (size_t)(ncol + 1) * tr * sizeof(T);
+  if (smem + ssmem > 48 * 1024) {
+    // cannot happen for k + 1 <= 64 columns: the 32-row floor needs 33 KB
+    set_error("cgs2: %zu + %zu bytes of shared memory exceed 48 KB", smem, ssmem);
+    return cudaErrorInvalidConfiguration;
+  }
+  const int grid = tma_grid<T, KMAX, KIND>(h, smem);
+  *grid_out = grid;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kRedThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (h->pdl_enabled && h->pdl_next && !h->profiling) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, cgs2_tma_kernel<T, KMAX, KIND>, Q, ns, ncol, w,
+                            (const double*)ws->h1, (const double*)ws->h2, qnew, tr,
+                            ws->partials, ws->counter, out, ws->dev_err);
+}
+
 template <typename T, int KIND>
 static int launch_pass(hpg_problem* h, const T* Q, long long ns, int ncol, const T* w, T* qnew,
-                       double* out, cudaStream_t s) {
+                       double* out, cudaStream_t s, int* grid_out) {
   static const int cls[3] = {K_CGS2_GEMVT, K_CGS2_REORTH, K_CGS2_FINAL};
-  Workspace* ws = h->ws;
   const double vecs = ncol + (KIND == kFinal ? 2 : 1);   // Q columns + w (+ q_new)
   const double bytes = (double)h->lev[0].n * vecs * sizeof(T);
-  return launch(h, cls[KIND], 0, prec_of<T>(), bytes, s, "cgs2_pass_kernel", [&] {
-    const double* a = ws->h1;
-    const double* b = ws->h2;
-    if (ncol <= 8)
-      return kl(h, cgs2_pass_kernel<T, 8, KIND>, ws->G, kRedThreads, s, Q, ns, ncol, w, a, b,
-                qnew, ws->partials, ws->counter, out);
-    if (ncol <= 16)
-      return kl(h, cgs2_pass_kernel<T, 16, KIND>, ws->G, kRedThreads, s, Q, ns, ncol, w, a, b,
-                qnew, ws->partials, ws->counter, out);
-    if (ncol <= 32)
-      return kl(h, cgs2_pass_kernel<T, 32, KIND>, ws->G, kRedThreads, s, Q, ns, ncol, w, a, b,
-                qnew, ws->partials, ws->counter, out);
-    return kl(h, cgs2_pass_kernel<T, 64, KIND>, ws->G, kRedThreads, s, Q, ns, ncol, w, a, b,
-              qnew, ws->partials, ws->counter, out);
+  return launch(h, cls[KIND], 0, prec_of<T>(), bytes, s, "cgs2_tma_kernel", [&] {
+    if (ncol <= 8) return enqueue_tma<T, 8, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
+    if (ncol <= 16) return enqueue_tma<T, 16, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
+    if (ncol <= 32) return enqueue_tma<T, 32, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
+    return enqueue_tma<T, 64, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
   });
 }
 
@@ -612,13 +717,14 @@ static int enqueue_step(hpg_problem* h, int k, hpg_prec prec, unsigned long long
   if ((rc = launch_spmv(h, 0, prec, z, w, s))) return rc;
   const int ncol = k + 1;
   T* qnew = Q + (long long)(k + 1) * ns;
-  if ((rc = launch_pass<T, kGemvT>(h, Q, ns, ncol, w, nullptr, ws->h1, s))) return rc;
-  if ((rc = launch_pass<T, kReorth>(h, Q, ns, ncol, w, nullptr, ws->h2, s))) return rc;
-  if ((rc = launch_pass<T, kFinal>(h, Q, ns, ncol, w, qnew, nullptr, s))) return rc;
+  int g_final = 0;
+  if ((rc = launch_pass<T, kGemvT>(h, Q, ns, ncol, w, nullptr, ws->h1, s, &g_final))) return rc;
+  if ((rc = launch_pass<T, kReorth>(h, Q, ns, ncol, w, nullptr, ws->h2, s, &g_final))) return rc;
+  if ((rc = launch_pass<T, kFinal>(h, Q, ns, ncol, w, qnew, nullptr, s, &g_final))) return rc;
   return launch(h, K_ARNOLDI_FINISH, 0, prec_of<T>(), 2.0 * h->lev[0].n * sizeof(T), s,
                 "arnoldi_finish_kernel", [&] {
                   return kl(h, arnoldi_finish_kernel<T>, ws->G, kRedThreads, s, qnew, ns,
-                            (const double*)ws->partials, ws->G / kCluster, k,
+                            (const double*)ws->partials, g_final / kCluster, k,
                             (const double*)ws->h1, (const double*)ws->h2, ws->H, ws->m + 1,
                             ws->cs, ws->sn, ws->t, ws->st, next);
                 });
@@ -663,7 +769,8 @@ static int enqueue_outer(hpg_problem* h, unsigned long long loop, cudaStream_t s
                   });
   if (rc) return rc;
   return launch(h, K_NORM, 0, HPG_FP64, 0.0, s, "outer_check_kernel", [&] {
-    return kl(h, outer_check_kernel, 1, 32, s, (const double*)ws->rho2, ws->st, loop);
+    return kl(h, outer_check_kernel, 1, 32, s, (const double*)ws->rho2, ws->st,
+              (const int*)ws->dev_err, loop);
   });
 }
 
@@ -749,8 +856,10 @@ static int capture_solve_graph(hpg_problem* h, int m, hpg_prec prec) {
   if (rc == HPG_OK) rc = append_conditional(h, s0, loop, cudaGraphCondTypeWhile, &body);
   cudaGraph_t g_end = nullptr;
   cudaError_t e = cudaStreamEndCapture(s0, &g_end);
-  if (rc) return rc;
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(main)", __FILE__, __LINE__);
+  if (rc || e != cudaSuccess) {
+    ws->graph = nullptr;   // a failed capture's graph is abandoned, not destroyed
+    return rc ? rc : cuda_fail(e, "cudaStreamEndCapture(main)", __FILE__, __LINE__);
+  }
   // WHILE body
   std::vector<cudaGraphConditionalHandle> hk(m);
   for (int k = 0; k < m; ++k) HPG_CK(cudaGraphConditionalHandleCreate(&hk[k], body, 0, 0));
@@ -785,9 +894,15 @@ static int capture_solve_graph(hpg_problem* h, int m, hpg_prec prec) {
   h->launches = launches_before;   // capture enqueues nothing that runs
   cudaGraph_t body_end = nullptr;
   e = cudaStreamEndCapture(s1, &body_end);
-  if (rc) return rc;
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(body)", __FILE__, __LINE__);
-  HPG_CK(cudaGraphInstantiate(&ws->exec, g, 0));
+  if (rc || e != cudaSuccess) {
+    ws->graph = nullptr;   // a failed capture's graph is abandoned, not destroyed
+    return rc ? rc : cuda_fail(e, "cudaStreamEndCapture(body)", __FILE__, __LINE__);
+  }
+  e = cudaGraphInstantiate(&ws->exec, g, 0);
+  if (e != cudaSuccess) {
+    ws->exec = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
   size_t nn = 0;
   cudaGraphGetNodes(g, nullptr, &nn);
   ws->graph_nodes = (int)nn;
@@ -903,6 +1018,11 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
   HPG_CK(cudaStreamSynchronize(s));
   h->pdl_next = false;
   const SolveState& fs = *ws->st_host;
+  if (fs.status == HPG_ERR_TIMEOUT) {
+    HPG_CK(cudaMemset(ws->dev_err, 0, 16));
+    status = HPG_ERR_TIMEOUT;
+    converged = false;
+  }
   if (info) {
     info->iterations = fs.iters;
     info->restarts = fs.restarts;

@@ -273,6 +273,7 @@ HPG_API const char* hpg_status_string(int status) {
     case HPG_ERR_ALLOC: return "HPG_ERR_ALLOC";
     case HPG_ERR_STATE: return "HPG_ERR_STATE";
     case HPG_ERR_UNSUPPORTED: return "HPG_ERR_UNSUPPORTED";
+    case HPG_ERR_TIMEOUT: return "HPG_ERR_TIMEOUT";
   }
   return "HPG_ERR_UNKNOWN";
 }
