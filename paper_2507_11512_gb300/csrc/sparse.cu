@@ -71,18 +71,19 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
 // launch.  Entries x_j with j >= valid_end read as zero: the first forward
 // sweep from z = 0 passes valid_end = start of the current colour block, so
 // that colours not yet visited count as zero without a memset.
-// 32 registers at most: eight 256-thread CTAs per SM, so the 1024 CTAs of a
-// 128^3 colour phase are resident in a single wave.
+//
+// Bandwidth variant, for levels whose matrix streams from HBM: 32 registers,
+// eight 256-thread CTAs per SM (a 128^3 colour phase is a single wave), the
+// matrix read evict-first.  Launched without programmatic overlap: measured on
+// GB300, letting the next phase's CTAs start early (or prefetching its slots
+// into L2) slows this bandwidth-bound chain down.
 template <typename T, bool STREAM>
 __global__ void __launch_bounds__(256, 8)
 gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                 const T* __restrict__ r, T* x, long long row0, long long nrows,
                 long long valid_end) {
-  pdl_trigger();
-  const long long t0 = blockIdx.x * (long long)blockDim.x;
-  prefetch_ell_rows(vals, cols, ns, row0 + t0, (int)min((long long)blockDim.x, nrows - t0));
   pdl_wait();
-  const long long t = t0 + threadIdx.x;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nrows) return;
   const long long row = row0 + t;
   T acc = r[row];
@@ -96,6 +97,41 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
   }
   const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
   x[row] = acc / diag;
+}
+
+// Latency variant, for coarse levels (matrix resident in L2, at most a few
+// tens of thousands of rows per phase): 64-thread CTAs spread the rows over
+// the SMs, and each thread loads its row's 27 indices and values *before* the
+// programmatic wait -- the matrix does not depend on earlier kernels -- so that
+// latency overlaps the previous phase; after the wait it issues all the
+// gathers of x at once.  Same slot order and arithmetic as gs_phase_kernel.
+template <typename T>
+__global__ void __launch_bounds__(64)
+gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
+                      const T* __restrict__ r, T* x, long long row0, long long nrows,
+                      long long valid_end) {
+  pdl_trigger();
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool live = t < nrows;
+  const long long row = row0 + (live ? t : 0);
+  int col[kSlots];
+  T a[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    col[s] = live ? __ldg(cols + s * ns + row) : 0;
+    a[s] = live ? __ldg(vals + s * ns + row) : T(1);
+  }
+  pdl_wait();
+  if (!live) return;
+  T xv[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s)
+    xv[s] = (s != kCentre && col[s] < valid_end) ? __ldg(x + col[s]) : T(0);
+  T acc = r[row];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s)
+    if (s != kCentre) acc = fma(-a[s], xv[s], acc);
+  x[row] = acc / a[kCentre];
 }
 
 // Fused residual + injection restriction (Sec. 3.2.4, last equation):
@@ -113,10 +149,6 @@ restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc
   const long long cnt = (long long)cx * cy * gf.cdz[kCoarseColour];
   const long long ns = gf.n_store;
   const long long p0 = blockIdx.x * (long long)blockDim.x;
-  // rows of the (32-row aligned) colour block, padded tail included
-  const long long nblk = gf.off[kCoarseColour + 1] - gf.off[kCoarseColour];
-  prefetch_ell_rows(vals, cols, ns, gf.off[kCoarseColour] + p0,
-                    (int)min((long long)blockDim.x, nblk - p0));
   pdl_wait();
   const long long p = p0 + threadIdx.x;
   if (p >= cnt) return;
@@ -214,10 +246,13 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
   const T* vals = Prec<T>::vals(L);
   return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32,
                 L.cnt[c] * bytes_gs_row(sizeof(T), sizeof(T)), s, "gs_phase_kernel", [&] {
-                  const bool stream = L.g.n_store * 27LL * 8 > kStreamMatrixBytes;
-                  return kl(h, stream ? gs_phase_kernel<T, true> : gs_phase_kernel<T, false>,
-                            grid_for(nrows, kThreads), kThreads, s, vals, L.cols, L.g.n_store, r,
-                            z, row0, nrows, valid_end);
+                  if (L.g.n_store * 27LL * 8 > kStreamMatrixBytes) {
+                    h->pdl_next = false;   // full serialisation (see gs_phase_kernel)
+                    return kl(h, gs_phase_kernel<T, true>, grid_for(nrows, kThreads), kThreads,
+                              s, vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                  }
+                  return kl(h, gs_phase_small_kernel<T>, grid_for(nrows, 64), 64, s, vals,
+                            L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
                 });
 }
 
