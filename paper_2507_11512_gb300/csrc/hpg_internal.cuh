@@ -109,6 +109,22 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Slots (bit s) a Gauss-Seidel phase of colour c reads.  Normally every slot;
+// in the first forward sweep from z = 0 only the diagonal and the slots whose
+// neighbour colour is below c: colours not yet visited are still zero, so
+// their entries need not even be loaded.  An odd offset along an axis flips
+// that axis's parity bit of the colour.
+__host__ __device__ inline unsigned gs_slot_mask(int c, bool from_zero) {
+  if (!from_zero) return (1u << 27) - 1u;
+  unsigned m = 1u << 13;
+  for (int s = 0; s < 27; ++s) {
+    const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+    const int nc = c ^ ((dx & 1) | ((dy & 1) << 1) | ((dz & 1) << 2));
+    if (nc < c) m |= 1u << s;
+  }
+  return m;
+}
+
 // One thread of the block prefetches the block's slice [row, row + rows) of
 // the 27 value and index slots of a slot-major ELL matrix.  row and rows are
 // multiples of 4 (colour blocks start on 32-row boundaries), so every range

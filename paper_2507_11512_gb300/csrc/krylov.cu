@@ -264,12 +264,20 @@ template <> struct Vec4<double> {
 //
 // Each CTA walks row tiles of TR rows (a multiple of 32).  Thread 0 streams a tile
 // of w and of the k+1 basis columns into shared memory with TMA bulk copies
-// (one per vector, completion counted on an mbarrier), double-buffered, so the
-// next tile is in flight while this one is used; threads then read the tile
+// (one per vector, completion counted on an mbarrier), kTmaStages deep, so the
+// next tiles are in flight while this one is used; threads then read the tile
 // from shared memory (row r of column j at stage[(j+1)*TR + r]: consecutive
 // threads, consecutive words).  A thread keeps only its k+1 accumulators.
-// The host picks TR so the two stages hold ~48 KB whatever k is.
+// The host picks TR so the stages fill ~48 KB whatever k is.
 enum PassKind { kGemvT = 0, kReorth = 1, kFinal = 2 };
+
+#ifndef HPG_TMA_STAGES
+#define HPG_TMA_STAGES 3
+#endif
+#ifndef HPG_TMA_SMEM_KB
+#define HPG_TMA_SMEM_KB 64
+#endif
+constexpr int kTmaStages = HPG_TMA_STAGES;   // tiles in flight per CTA
 
 template <typename T, int KMAX, int KIND>
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kRedThreads)
@@ -278,17 +286,16 @@ cgs2_tma_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __rest
                 T* __restrict__ qnew, int TR, double* __restrict__ partials,
                 unsigned int* counter, double* __restrict__ out, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char tma_smem[];
-  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ __align__(8) unsigned long long bar[kTmaStages];
   __shared__ T sh1[KMAX], sh2[KMAX];
   __shared__ int s_abort;
   pdl_trigger();
   const int tid = threadIdx.x;
   const long long ntiles = (ns + TR - 1) / TR;
-  T* const stage0 = reinterpret_cast<T*>(tma_smem);
-  T* const stage1 = stage0 + (long long)(ncol + 1) * TR;
+  const long long stage_elems = (long long)(ncol + 1) * TR;
+  T* const smem0 = reinterpret_cast<T*>(tma_smem);
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int i = 0; i < kTmaStages; ++i) mbar_init(&bar[i], 1);
     fence_mbar_init();
     s_abort = 0;
   }
@@ -300,32 +307,35 @@ cgs2_tma_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __rest
     }
   }
   __syncthreads();
-  // thread 0: bring tile t into stage s
+  // warp 0: bring tile t into stage sidx.  Lane 0 posts the expected bytes;
+  // the lanes issue the ncol+1 copies in parallel (a copy may land before
+  // the expectation is posted: the transaction count goes negative meanwhile).
   auto issue = [&](long long t, int sidx) {
     if (t >= ntiles) return;
     const long long r0 = t * TR;
     const long long rows = ns - r0 < TR ? ns - r0 : TR;
     const unsigned bytes = (unsigned)(rows * sizeof(T));
-    T* const dst = sidx ? stage1 : stage0;
-    unsigned long long* const b = sidx ? &bar[1] : &bar[0];
-    mbar_expect_tx(b, bytes * (unsigned)(ncol + 1));
-    bulk_g2s(dst, w + r0, bytes, b);
-    for (int j = 0; j < ncol; ++j) bulk_g2s(dst + (long long)(j + 1) * TR, Q + j * ns + r0, bytes, b);
+    T* const dst = smem0 + sidx * stage_elems;
+    unsigned long long* const b = &bar[sidx];
+    const int lane = tid & 31;
+    if (lane == 0) mbar_expect_tx(b, bytes * (unsigned)(ncol + 1));
+    for (int v = lane; v <= ncol; v += 32) {
+      const T* src = v == 0 ? w + r0 : Q + (v - 1) * ns + r0;
+      bulk_g2s(dst + (long long)v * TR, src, bytes, b);
+    }
   };
-  if (tid == 0) {
-    issue(blockIdx.x, 0);
-    issue(blockIdx.x + gridDim.x, 1);
-  }
+  if (tid < 32)
+    for (int i = 0; i < kTmaStages; ++i) issue(blockIdx.x + (long long)i * gridDim.x, i);
   T acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = T(0);
-  unsigned phase0 = 0u, phase1 = 0u;
+  unsigned phases = 0u;   // bit i: parity of stage i
   int sidx = 0;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const bool ok = sidx ? mbar_wait(&bar[1], phase1) : mbar_wait(&bar[0], phase0);
+    const bool ok = mbar_wait(&bar[sidx], (phases >> sidx) & 1u);
     if (!ok) s_abort = 1;
-    if (sidx) phase1 ^= 1u; else phase0 ^= 1u;
-    const T* st = sidx ? stage1 : stage0;
+    phases ^= 1u << sidx;
+    const T* st = smem0 + sidx * stage_elems;
     const int rows = (int)(ns - t * TR < TR ? ns - t * TR : TR);
     if (ok) {
       for (int r = tid; r < rows; r += kRedThreads) {
@@ -360,19 +370,18 @@ cgs2_tma_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __rest
     }
     __syncthreads();   // every thread is done with this stage (and s_abort is seen)
     if (s_abort) break;
-    if (tid == 0) {
+    if (tid < 32) {
       fence_proxy_async_smem();
-      issue(t + 2LL * gridDim.x, sidx);
+      issue(t + (long long)kTmaStages * gridDim.x, sidx);
     }
-    sidx ^= 1;
+    sidx = sidx + 1 == kTmaStages ? 0 : sidx + 1;
   }
   if (s_abort) {
     // a copy never completed: flag it, give the copies in flight a bounded
     // chance to land before the CTA's shared memory goes away
     if (tid == 0) {
       atomicExch(err, 1);
-      mbar_wait(&bar[0], phase0);
-      mbar_wait(&bar[1], phase1);
+      for (int i = 0; i < kTmaStages; ++i) mbar_wait(&bar[i], (phases >> i) & 1u);
     }
     __syncthreads();
   }
@@ -612,20 +621,24 @@ __global__ void delay_kernel(long long cycles) {
 // ----------------------------------------------------------------- launchers
 template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? HPG_FP64 : HPG_FP32; }
 
-// Tile rows: two stages of (w + ncol columns) x TR in the shared memory a
+// Tile rows: kTmaStages stages of (w + ncol columns) x TR in the shared memory a
 // CTA may use without opting in (48 KB) minus the kernel's static shared
 // memory; TR a multiple of 32 in [32, 2048] (16-byte aligned copies and
 // sizes).
+constexpr long long kTmaSmemBytes = HPG_TMA_SMEM_KB * 1024LL;   // opted-in shared memory per CTA
+
 template <typename T>
 static int tma_rows(int ncol, size_t static_smem) {
-  const long long per_row = 2LL * (ncol + 1) * sizeof(T);
-  const long long budget = 48LL * 1024 - (long long)static_smem - 256;
+  const long long per_row = (long long)kTmaStages * (ncol + 1) * sizeof(T);
+  const long long budget = kTmaSmemBytes - (long long)static_smem - 256;
   long long tr = budget / per_row / 32 * 32;
   if (tr < 32) tr = 32;
   if (tr > 2048) tr = 2048;
   return (int)tr;
 }
 
+// Static shared memory of an instantiation; also opts it into
+// kTmaSmemBytes of shared memory per CTA (once per process and device).
 template <typename T, int KMAX, int KIND>
 static size_t tma_static_smem() {
   static size_t bytes = 0;
@@ -634,6 +647,9 @@ static size_t tma_static_smem() {
     bytes = cudaFuncGetAttributes(&a, cgs2_tma_kernel<T, KMAX, KIND>) == cudaSuccess
                 ? a.sharedSizeBytes
                 : 16384;
+    cudaFuncSetAttribute(cgs2_tma_kernel<T, KMAX, KIND>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kTmaSmemBytes - (long long)bytes));
     cudaGetLastError();
   }
   return bytes;
@@ -663,10 +679,10 @@ static cudaError_t enqueue_tma(hpg_problem* h, const T* Q, long long ns, int nco
   Workspace* ws = h->ws;
   const size_t ssmem = tma_static_smem<T, KMAX, KIND>();
   const int tr = tma_rows<T>(ncol, ssmem);
-  const size_t smem = 2 * (size_t)(ncol + 1) * tr * sizeof(T);
-  if (smem + ssmem > 48 * 1024) {
-    // cannot happen for k + 1 <= 64 columns: the 32-row floor needs 33 KB
-    set_error("cgs2: %zu + %zu bytes of shared memory exceed 48 KB", smem, ssmem);
+  const size_t smem = (size_t)kTmaStages * (ncol + 1) * tr * sizeof(T);
+  if ((long long)(smem + ssmem) > kTmaSmemBytes) {
+    // cannot happen for k + 1 <= 64 columns: the 32-row floor needs 50 KB at most
+    set_error("cgs2: %zu + %zu bytes of shared memory exceed %lld", smem, ssmem, kTmaSmemBytes);
     return cudaErrorInvalidConfiguration;
   }
   const int grid = tma_grid<T, KMAX, KIND>(h, smem);

@@ -77,11 +77,11 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
 // matrix read evict-first.  Launched without programmatic overlap: measured on
 // GB300, letting the next phase's CTAs start early (or prefetching its slots
 // into L2) slows this bandwidth-bound chain down.
-template <typename T, bool STREAM>
+template <typename T, bool STREAM, bool MASKED>
 __global__ void __launch_bounds__(256, 8)
 gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                 const T* __restrict__ r, T* x, long long row0, long long nrows,
-                long long valid_end) {
+                long long valid_end, unsigned mask) {
   pdl_wait();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nrows) return;
@@ -90,10 +90,23 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     if (s == kCentre) continue;
-    const T a = ld_matrix<STREAM>(vals + s * ns + row);
-    const int c = ld_matrix<STREAM>(cols + s * ns + row);
-    const T xv = (c < valid_end) ? __ldg(x + c) : T(0);
-    acc = fma(-a, xv, acc);
+    if (MASKED) {
+      // slots outside `mask` are known zero: predicated off, not loaded
+      const bool use = (mask >> s) & 1u;
+      T a = T(0);
+      int c = 0;
+      if (use) {
+        a = ld_matrix<STREAM>(vals + s * ns + row);
+        c = ld_matrix<STREAM>(cols + s * ns + row);
+      }
+      const T xv = (use && c < valid_end) ? __ldg(x + c) : T(0);
+      acc = fma(-a, xv, acc);
+    } else {
+      const T a = ld_matrix<STREAM>(vals + s * ns + row);
+      const int c = ld_matrix<STREAM>(cols + s * ns + row);
+      const T xv = (c < valid_end) ? __ldg(x + c) : T(0);
+      acc = fma(-a, xv, acc);
+    }
   }
   const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
   x[row] = acc / diag;
@@ -187,13 +200,14 @@ prolong_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
 
 // ----------------------------------------------------------------- launchers
 constexpr int kThreads = 256;
+constexpr long long kPdlSmallRows = 16384;   // latency-variant phases overlapped up to this
 
 // Algorithmic DRAM bytes per row (ELL with 27 padded slots, int32 indices;
 // every vector entry read or written once).  sv / sx: value / vector bytes.
 static double bytes_spmv_row(double sv, double sx) { return 27.0 * (sv + 4.0) + 2.0 * sx; }
-// GS phase: 27 values, 26 indices (the diagonal's is implied), r_i, the new
-// x_i, and x gathered once.
-static double bytes_gs_row(double sv, double sx) { return 27.0 * sv + 26.0 * 4.0 + 3.0 * sx; }
+// GS phase, per row reading k off-diagonal slots: k + 1 values, k indices
+// (the diagonal's is implied), r_i, the new x_i, and x gathered once (in
+// proportion to the slots read).
 static double bytes_restrict_row(double sv, double sx) { return 27.0 * (sv + 4.0) + 3.0 * sx; }
 
 template <typename T>
@@ -244,13 +258,21 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
   if (nrows == 0) return HPG_OK;
   const long long valid_end = from_zero ? row0 : L.g.n_store;
   const T* vals = Prec<T>::vals(L);
-  return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32,
-                L.cnt[c] * bytes_gs_row(sizeof(T), sizeof(T)), s, "gs_phase_kernel", [&] {
+  const int nslots = __builtin_popcount(gs_slot_mask(c, from_zero)) - 1;   // off-diagonal
+  const double row_bytes =
+      (nslots + 1.0) * sizeof(T) + nslots * 4.0 + (2.0 + nslots / 26.0) * sizeof(T);
+  return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32, L.cnt[c] * row_bytes, s,
+                "gs_phase_kernel", [&] {
                   if (L.g.n_store * 27LL * 8 > kStreamMatrixBytes) {
                     h->pdl_next = false;   // full serialisation (see gs_phase_kernel)
-                    return kl(h, gs_phase_kernel<T, true>, grid_for(nrows, kThreads), kThreads,
-                              s, vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                    return kl(h, from_zero ? gs_phase_kernel<T, true, true>
+                                           : gs_phase_kernel<T, true, false>,
+                              grid_for(nrows, kThreads), kThreads, s, vals, L.cols, L.g.n_store,
+                              r, z, row0, nrows, valid_end, gs_slot_mask(c, from_zero));
                   }
+                  // measured on GB300: programmatic overlap helps the smallest
+                  // phases and slows phases of tens of thousands of rows
+                  if (nrows > kPdlSmallRows) h->pdl_next = false;
                   return kl(h, gs_phase_small_kernel<T>, grid_for(nrows, 64), 64, s, vals,
                             L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
                 });
