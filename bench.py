@@ -31,6 +31,30 @@ if ROOT not in sys.path:
 METRIC = "GMRES-IR GFLOP/s and time-to-1e-9 residual, MxP vs FP64, 1 GB300; % HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM bytes (read + write) per launch of the level-0 FP32 Gauss-Seidel phase
+# kernel at 128^3, from one ncu capture (profiles/gs_phase_level0_128cube.md),
+# valid while the kernel sources hash to `sources_sha256`.
+GS_TRAFFIC = {"bytes_per_launch": 65346048.0,
+              "sources_sha256": "54d71c2ac4eb47e887c92c558329833224c2f8152e9840df9cb2a445b64a9798"}
+GS_SOURCES = ("paper_2507_11512_gb300/csrc/sparse.cu", "paper_2507_11512_gb300/csrc/hpg_internal.cuh")
+
+
+def gs_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in GS_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def gs_traffic():
+    """Captured DRAM traffic per launch, or None if the kernel changed since."""
+    if GS_TRAFFIC["bytes_per_launch"] is None:
+        return None
+    return GS_TRAFFIC["bytes_per_launch"] if gs_sources_sha256() == GS_TRAFFIC[
+        "sources_sha256"] else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -274,13 +298,48 @@ def run_gpu(args):
     tot_ms = sum(p["total_ms"] for p in prof)
     prof.sort(key=lambda p: -p["total_ms"])
     peak, peak_src = measured_peaks()
-    top = prof[0]
-    dom_gbs = top["bytes"] / (top["total_ms"] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "%s (level %d, %s)" % (
-                    top["name"], top["level"], "fp32" if top["prec"] == 1 else "fp64"),
-                "achieved": dom_gbs, "peak": peak, "unit": "GB/s", "frac": dom_gbs / peak,
-                "peak_source": peak_src, "traffic": None,
-                "launches": top["launches"], "avg_launch_us": 1e3 * top["total_ms"] / top["launches"]}
+
+    # ---- dominant kernel (level-0 FP32 Gauss-Seidel phase) timed with CUDA
+    # events on the launching stream, launched exactly as the V-cycle launches
+    # it: hpg_mg_smooth = 15 colour phases per sweep (colours 0..7, 6..0),
+    # captured in a CUDA graph like the solve's own launches
+    gs_reps = 20
+    info0 = prob.info[0]
+    r_gs = prob.to_storage(torch.randn(n, dtype=torch.float64, device=dev,
+                                       generator=torch.Generator(device=dev).manual_seed(1)),
+                           dtype=torch.float32)
+    z_gs = torch.zeros_like(r_gs)
+    for _ in range(3):
+        hpg.mg_smooth(prob.h, 0, r_gs, z_gs, 1, False)
+    torch.cuda.synchronize()
+    gs_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gs_graph):
+        for _ in range(gs_reps):
+            hpg.mg_smooth(prob.h, 0, r_gs, z_gs, 1, False)
+    gs_graph.replay()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    gs_graph.replay()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gs_ms = g0.elapsed_time(g1)
+    del gs_graph
+    cnt = info0["colour_count"]
+    gs_row_bytes = metrics.gs_row_bytes(4, 4)
+    gs_phases = 15
+    gs_bytes = (sum(cnt) + sum(cnt[:7])) * gs_row_bytes * gs_reps
+    gs_gbs = gs_bytes / (gs_ms / 1e3) / 1e9
+    traffic = gs_traffic()
+    roofline = {"bound": "hbm", "kernel": "gs_phase_kernel (level 0, fp32)",
+                "achieved": gs_gbs, "peak": peak, "unit": "GB/s", "frac": gs_gbs / peak,
+                "peak_source": peak_src,
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": gs_bytes / (gs_reps * gs_phases),
+                "launches": gs_reps * gs_phases,
+                "avg_launch_us": 1e3 * gs_ms / (gs_reps * gs_phases),
+                "timing": "CUDA events around a graph of %d hpg_mg_smooth sweeps on level 0 "
+                          "(%d phase launches)" % (gs_reps, gs_reps * gs_phases)}
     kernels = [{"name": p["name"], "level": p["level"], "prec": p["prec"],
                 "launches": p["launches"], "share": p["total_ms"] / tot_ms,
                 "avg_us": 1e3 * p["total_ms"] / p["launches"],

@@ -157,6 +157,23 @@ HPG_API int hpg_spmv(hpg_problem_t* h, int level, hpg_prec prec,
 HPG_API int hpg_mg_vcycle(hpg_problem_t* h, int level, hpg_prec prec,
                           const void* r, void* z, void* stream);
 
+/* `sweeps` symmetric multicolour Gauss-Seidel sweeps on `level` (eqs. (1)-(2),
+ * Sec. 3.2.1 -- the smoother of the V-cycle, launched exactly as the V-cycle
+ * launches it): each sweep updates the colours 0..7, then 7..0, with
+ * z_i <- (r_i - sum_{j != i} a_ij z_j) / a_ii for every row i of the colour;
+ * a colour phase that would repeat the previous one on unchanged data (at the
+ * forward/backward turn and between sweeps) is skipped, which changes no value.
+ * z_is_zero != 0: z enters as 0 and its contents are never read (the first
+ * forward sweep omits the zero terms); otherwise z holds the initial iterate.
+ * sweeps = 0 leaves z unchanged (or zeroes it when z_is_zero).  prec HPG_FP64
+ * or HPG_FP32.  r, z: device, storage order, length n_store, must not
+ * overlap; padding rows of z stay 0 if they enter 0.  Requires
+ * hpg_build_mg_hierarchy.  HPG_ERR_INVALID for a bad level, precision,
+ * sweep count or pointer.  Asynchronous on `stream`. */
+HPG_API int hpg_mg_smooth(hpg_problem_t* h, int level, hpg_prec prec,
+                          const void* r, void* z, int sweeps, int z_is_zero,
+                          void* stream);
+
 /* Allocation-free V-cycle.  The paper has no counterpart: this is an entry
  * point for callers that cannot allocate device memory when they call --
  * code running inside a CUDA stream capture (cudaMalloc is not allowed there),

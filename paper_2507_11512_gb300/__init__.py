@@ -16,7 +16,7 @@ from ._lib import (HPG_BF16, HPG_ERR_ALLOC, HPG_ERR_BREAKDOWN, HPG_ERR_CUDA,  # 
                    KernelStat, LevelDesc, SolveInfo, StencilParams, check, load)
 
 __all__ = ["setup_problem", "build_mg_hierarchy", "num_levels", "level_info", "permute",
-           "spmv", "mg_vcycle", "gmres_ir_solve", "destroy", "set_profiling", "set_execution",
+           "spmv", "mg_vcycle", "mg_smooth", "gmres_ir_solve", "destroy", "set_profiling", "set_execution",
            "set_option",
            "profile_report", "Problem", "HpgError",
            "HPG_FP64", "HPG_FP32", "HPG_BF16", "HPG_FP16", "load"]
@@ -110,6 +110,16 @@ def mg_vcycle(h, level, r, z, stream=None):
         raise TypeError("r and z must have the same dtype")
     check(load().hpg_mg_vcycle(h, level, p, _ptr(r), _ptr(z), _stream(stream)),
           "hpg_mg_vcycle")
+
+
+def mg_smooth(h, level, r, z, sweeps=1, z_is_zero=False, stream=None):
+    """hpg_mg_smooth: `sweeps` symmetric multicolour Gauss-Seidel sweeps on z
+    (storage order; z_is_zero: z enters as 0 and is not read)."""
+    p = _prec_of(r)
+    if _prec_of(z) != p:
+        raise TypeError("r and z must have the same dtype")
+    check(load().hpg_mg_smooth(h, level, p, _ptr(r), _ptr(z), int(sweeps), 1 if z_is_zero else 0,
+                               _stream(stream)), "hpg_mg_smooth")
 
 
 def gmres_ir_solve(h, b, x, tol=1e-9, restart=30, maxit=10000, inner=HPG_FP32, basis=None,
@@ -216,6 +226,16 @@ class Problem:
         z = _torch().empty_like(r_st)
         mg_vcycle(self.h, level, r_st, z)
         return z
+
+    def smooth(self, r_st, z_st=None, level=0, sweeps=1):
+        """Symmetric Gauss-Seidel sweeps on z_st in place (from z = 0 when
+        z_st is None); returns z."""
+        if z_st is None:
+            z = _torch().empty_like(r_st)
+            mg_smooth(self.h, level, r_st, z, sweeps, True)
+            return z
+        mg_smooth(self.h, level, r_st, z_st, sweeps, False)
+        return z_st
 
     def solve(self, b, x=None, **kw):
         torch = _torch()

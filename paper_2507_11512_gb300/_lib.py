@@ -65,6 +65,7 @@ SIGNATURES = {
     "hpg_permute": (_I, [_P, _I, _I, _I, _P, _I, _P, _P]),
     "hpg_spmv": (_I, [_P, _I, _I, _P, _P, _P]),
     "hpg_mg_vcycle": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hpg_mg_smooth": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
     "hpg_mg_vcycle_noalloc": (_I, [_P, _I, _I, _P, _P, _P]),
     "hpg_gmres_ir_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(SolveInfo), _P]),
     "hpg_set_profiling": (_I, [_P, _I]),

@@ -139,56 +139,6 @@ __device__ __forceinline__ void prefetch_ell_rows(const TV* vals, const int* col
   }
 }
 
-// ------------------------------------------------- TMA bulk copies, mbarriers
-// 1D bulk copies global -> shared by the TMA engine, completion counted in
-// bytes on a shared-memory mbarrier.  Addresses must be 16-byte aligned and
-// sizes multiples of 16 bytes.
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// Orders this thread's earlier generic-proxy accesses to shared memory before
-// later async-proxy (TMA) writes to it.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the given phase parity; false if the limit ran out.
-constexpr unsigned kMbarWaitLimit = 1u << 22;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
-  for (unsigned it = 0; it < kMbarWaitLimit; ++it)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
-}
-
 // ------------------------------------------------------------ host objects
 struct Level {
   Geom g;
@@ -211,7 +161,7 @@ struct Profiler;    // per-kernel-class CUDA-event timing (profile.cu)
 // Kernel classes reported by the profiler.
 enum KernelClass {
   K_GEN = 0, K_PERMUTE, K_SPMV, K_RESIDUAL, K_GS, K_RESTRICT, K_PROLONG, K_CGS2_GEMVT,
-  K_CGS2_REORTH, K_CGS2_FINAL, K_ARNOLDI_FINISH, K_TRSM, K_COMBINE, K_UPDATE_X,
+  K_CGS2_REORTH, K_CGS2_FINAL, K_ARNOLDI_SCALE, K_TRSM, K_COMBINE, K_UPDATE_X,
   K_CYCLE_START, K_NORM, K_VCYCLE, K_NUM_CLASSES
 };
 const char* kernel_class_name(int cls);

@@ -8,7 +8,6 @@
 // per-thread accumulation in T; block and global sums, H, the rotations, t, y,
 // the outer residual, its norm and x are FP64.
 
-#include <cooperative_groups.h>
 #include <math.h>
 #include <string.h>
 
@@ -16,14 +15,12 @@
 
 #include "hpg_internal.cuh"
 
-namespace cg = cooperative_groups;
 
 namespace hpg {
 
 constexpr int kRedThreads = 256;   // threads of every reduction kernel
 constexpr int kWarps = kRedThreads / 32;
 constexpr int kPartStride = 64;    // partials row stride (>= max columns)
-constexpr int kCluster = 8;        // CTAs per cluster of the reduction kernels
 
 struct SolveState {
   double rho0;    // ||b||_2
@@ -105,13 +102,12 @@ static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec) {
   const size_t es = prec_size(prec);
   ws->m = m;
   ws->prec = prec;
-  // reduction grids: up to 8 CTAs per SM, in whole clusters (the TMA passes
-  // use as many resident clusters as fit, at most G)
+  // reduction grids: up to 8 blocks per SM (the CGS2 passes use one wave of
+  // resident blocks, at most G)
   long long g = (ns + kRedThreads - 1) / kRedThreads;
   const long long gmax = 8LL * h->num_sms;
   if (g > gmax) g = gmax;
-  g = (g + kCluster - 1) / kCluster * kCluster;
-  ws->G = (int)(g < kCluster ? kCluster : g);
+  ws->G = (int)(g < 1 ? 1 : g);
   int rc = HPG_OK;
   rc = rc ? rc : dev_alloc(&ws->Q, es * ns * (m + 1));
   rc = rc ? rc : dev_alloc(&ws->z, es * ns);
@@ -154,71 +150,6 @@ __device__ __forceinline__ A warp_sum(A v) {
   return v;
 }
 
-// Reduces acc[0..nred) over the block, then over the block's cluster of
-// kCluster CTAs through distributed shared memory; rank 0 of each cluster
-// stores the cluster's sums in partials[cluster][.].  When `out` is given, the
-// last cluster to finish (atomic ticket) sums all cluster partials in a fixed
-// order into out[0..nred).  Deterministic for a fixed grid.
-template <typename A, int KMAX>
-__device__ void reduce_publish(const A (&acc)[KMAX], int nred, double* __restrict__ partials,
-                               unsigned int* counter, double* __restrict__ out) {
-  __shared__ double red[kWarps][KMAX];
-  __shared__ double blk[KMAX];
-  __shared__ double red2[kRedThreads];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) {
-    if (j < nred) {
-      const A v = warp_sum(acc[j]);
-      if (lane == 0) red[warp][j] = (double)v;
-    }
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < nred; j += kRedThreads) {
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < kWarps; ++q) s += red[q][j];
-    blk[j] = s;
-  }
-  cg::cluster_group cluster = cg::this_cluster();
-  cluster.sync();
-  const unsigned rank = cluster.block_rank();
-  const long long cid = blockIdx.x / kCluster;
-  if (rank == 0) {
-    for (int j = threadIdx.x; j < nred; j += kRedThreads) {
-      double s = blk[j];
-      for (int r = 1; r < kCluster; ++r) s += *cluster.map_shared_rank(&blk[j], r);
-      partials[cid * kPartStride + j] = s;
-    }
-  }
-  cluster.sync();   // siblings keep their shared memory until rank 0 has read it
-  if (rank != 0 || !out) return;
-  __threadfence();
-  __syncthreads();
-  const unsigned nclusters = gridDim.x / kCluster;
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == nclusters - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  constexpr int groups = kRedThreads / KMAX;
-  const int j = threadIdx.x % KMAX, grp = threadIdx.x / KMAX;
-  double s = 0.0;
-  if (j < nred) {
-#pragma unroll 4
-    for (int b = grp; b < (int)nclusters; b += groups)
-      s += __ldcg(partials + (long long)b * kPartStride + j);
-  }
-  red2[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x < nred) {
-    double tsum = 0.0;
-    for (int q = 0; q < groups; ++q) tsum += red2[q * KMAX + threadIdx.x];
-    out[threadIdx.x] = tsum;
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-}
-
 // ------------------------------------------------------------ vector access
 // Four consecutive rows of a vector (16-byte aligned: storage rows come in
 // multiples of 32).  Streaming variants for data read once, L2 variants for
@@ -258,208 +189,271 @@ template <> struct Vec4<double> {
 // Pass kinds of the three-pass CGS2 (Algorithm 3, CGS2 procedure):
 //   kGemvT:   h1 = Q^T w                                     (GEMVT)
 //   kReorth:  h2 = Q^T (w - Q h1)                            (GEMV + reorth GEMVT)
-//   kFinal:   q_new = (w - Q h1) - Q h2, partial ||q_new||^2  (reorth GEMV + norm)
+//   kFinal:   q_new = (w - Q h1) - Q h2, ||q_new||^2,        (reorth GEMV + norm)
+//             then (last block) the Arnoldi column and the Givens update
 // The GEMV w - Q h1 is recomputed row-locally in the last pass (same code,
 // same rounding) instead of being stored.
 //
-// Each CTA walks row tiles of TR rows (a multiple of 32).  Thread 0 streams a tile
-// of w and of the k+1 basis columns into shared memory with TMA bulk copies
-// (one per vector, completion counted on an mbarrier), kTmaStages deep, so the
-// next tiles are in flight while this one is used; threads then read the tile
-// from shared memory (row r of column j at stage[(j+1)*TR + r]: consecutive
-// threads, consecutive words).  A thread keeps only its k+1 accumulators.
-// The host picks TR so the stages fill ~48 KB whatever k is.
+// Each pass streams w and the k+1 basis columns once.  A thread takes a row
+// group of V consecutive rows per grid-stride iteration and issues one
+// 16/8/4-byte load per column for it before using any of them (KMAX x V
+// values in registers), so a resident warp keeps k+2 coalesced loads in
+// flight; it keeps only the k+1 accumulators across iterations.  Per-thread
+// sums are in T; warp, block and grid sums in FP64.  The grid sum is
+// deterministic: every block stores its partial sums, and the last block to
+// finish (atomic ticket) adds them in block order.
 enum PassKind { kGemvT = 0, kReorth = 1, kFinal = 2 };
 
-#ifndef HPG_TMA_STAGES
-#define HPG_TMA_STAGES 3
-#endif
-#ifndef HPG_TMA_SMEM_KB
-#define HPG_TMA_SMEM_KB 64
-#endif
-constexpr int kTmaStages = HPG_TMA_STAGES;   // tiles in flight per CTA
+// Rows per thread per iteration: the basis values of a row group (KMAX x V
+// elements) take at most 64 registers up to KMAX = 32 (FP32 and FP64).
+template <typename T, int KMAX>
+__host__ __device__ constexpr int pass_vec() {
+  return sizeof(T) == 4 ? (KMAX <= 16 ? 4 : KMAX <= 32 ? 2 : 1) : (KMAX <= 8 ? 2 : 1);
+}
+// Resident blocks per SM the register budget is sized for.
+template <typename T, int KMAX>
+__host__ __device__ constexpr int pass_min_blocks() {
+  return (sizeof(T) == 4 ? KMAX <= 32 : KMAX <= 16) ? 2 : 1;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void ld_group(const T* p, T (&v)[V]) {
+  if constexpr (sizeof(T) * V == 16) {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    memcpy(v, &t, 16);
+  } else if constexpr (sizeof(T) * V == 8) {
+    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+    memcpy(v, &t, 8);
+  } else {
+    v[0] = __ldcs(p);
+  }
+}
+template <typename T, int V>
+__device__ __forceinline__ void st_group(T* p, const T (&v)[V]) {
+  if constexpr (sizeof(T) * V == 16) {
+    float4 t;
+    memcpy(&t, v, 16);
+    *reinterpret_cast<float4*>(p) = t;
+  } else if constexpr (sizeof(T) * V == 8) {
+    float2 t;
+    memcpy(&t, v, 8);
+    *reinterpret_cast<float2*>(p) = t;
+  } else {
+    *p = v[0];
+  }
+}
+
+// Block sums of acc[0..nred) (FP64), stored as this block's partials; the last
+// block to arrive adds all blocks' partials in block order into sums[] (shared)
+// and returns true.  Every thread of the block must call it.
+template <typename A, int KMAX>
+__device__ bool block_partials_last(const A (&acc)[KMAX], int nred, double* __restrict__ partials,
+                                    unsigned int* counter, double* sums) {
+  __shared__ double red[kWarps][KMAX];
+  __shared__ double red2[kRedThreads];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < nred) {
+      const A v = warp_sum(acc[j]);
+      if (lane == 0) red[warp][j] = (double)v;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nred; j += kRedThreads) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) s += red[q][j];
+    partials[(long long)blockIdx.x * kPartStride + j] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  constexpr int groups = kRedThreads / KMAX;
+  const int j = threadIdx.x % KMAX, grp = threadIdx.x / KMAX;
+  double s = 0.0;
+  if (j < nred) {
+#pragma unroll 4
+    for (int b = grp; b < (int)gridDim.x; b += groups)
+      s += __ldcg(partials + (long long)b * kPartStride + j);
+  }
+  red2[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < nred) {
+    double tsum = 0.0;
+    for (int q = 0; q < groups; ++q) tsum += red2[q * KMAX + threadIdx.x];
+    sums[threadIdx.x] = tsum;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
+}
+
+// Arnoldi column and Givens update of Algorithm 3 for inner step k, run by
+// one warp: H[:,k] = h1 + h2, H[k+1,k] = beta; rotations 0..k-1 applied to
+// the column, rotation k formed to zero H[k+1,k], t updated, rho = |t[k+1]|.
+// The column and the rotations are staged in shared memory so the serial
+// recurrence runs on shared-memory operands.  In graph mode the next step's
+// IF node (handle `next`) is opened while the cycle stays active.
+template <int KMAX>
+__device__ void arnoldi_givens_warp(double beta, int k, const double* __restrict__ h1,
+                                    const double* __restrict__ h2, double* __restrict__ H,
+                                    int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                                    double* __restrict__ t, SolveState* st,
+                                    unsigned long long next) {
+  __shared__ double hs[KMAX + 1], css[KMAX], sns[KMAX];
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j <= k; j += 32) {
+    hs[j] = h1[j] + h2[j];
+    if (j < k) {
+      css[j] = cs[j];
+      sns[j] = sn[j];
+    }
+  }
+  if (lane == 0) hs[k + 1] = beta;
+  __syncwarp();
+  if (lane == 0) {
+    st->beta = beta;
+    bool go = false;
+    if (!isfinite(beta)) {
+      st->status = HPG_ERR_NAN;
+      st->active = 0;
+    } else {
+      for (int j = 0; j < k; ++j) {
+        const double a = hs[j], b = hs[j + 1];
+        hs[j] = css[j] * a + sns[j] * b;
+        hs[j + 1] = -sns[j] * a + css[j] * b;
+      }
+      const double mu = hypot(hs[k], hs[k + 1]);
+      if (!(mu > 0.0) || !isfinite(mu)) {
+        st->status = isfinite(mu) ? HPG_ERR_BREAKDOWN : HPG_ERR_NAN;
+        st->active = 0;
+      } else {
+        const double c = hs[k] / mu, sv = hs[k + 1] / mu;
+        cs[k] = c;
+        sn[k] = sv;
+        hs[k] = mu;
+        hs[k + 1] = 0.0;
+        const double tk = t[k];
+        t[k + 1] = -sv * tk;
+        t[k] = c * tk;
+        const double rho = fabs(-sv * tk);
+        st->rho = rho;
+        st->k = k + 1;
+        st->iters += 1;
+        go = !(rho / st->rho0 < st->tol || st->iters >= st->maxit || k + 1 >= st->m);
+        st->active = go ? 1 : 0;
+      }
+    }
+    if (next) cudaGraphSetConditional(next, go ? 1u : 0u);
+  }
+  __syncwarp();
+  double* hc = H + (long long)k * ldh;
+  for (int j = lane; j <= k + 1; j += 32) hc[j] = hs[j];
+}
 
 template <typename T, int KMAX, int KIND>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kRedThreads)
-cgs2_tma_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __restrict__ w,
-                const double* __restrict__ h1, const double* __restrict__ h2,
-                T* __restrict__ qnew, int TR, double* __restrict__ partials,
-                unsigned int* counter, double* __restrict__ out, int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char tma_smem[];
-  __shared__ __align__(8) unsigned long long bar[kTmaStages];
+__global__ void __launch_bounds__(kRedThreads, (pass_min_blocks<T, KMAX>()))
+cgs2_pass_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __restrict__ w,
+                 const double* __restrict__ h1, const double* __restrict__ h2,
+                 T* __restrict__ qnew, double* __restrict__ partials, unsigned int* counter,
+                 double* __restrict__ out, double* __restrict__ H, int ldh,
+                 double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ t,
+                 SolveState* st, unsigned long long next) {
+  constexpr int V = pass_vec<T, KMAX>();
   __shared__ T sh1[KMAX], sh2[KMAX];
-  __shared__ int s_abort;
+  __shared__ double sums[KMAX];
   pdl_trigger();
-  const int tid = threadIdx.x;
-  const long long ntiles = (ns + TR - 1) / TR;
-  const long long stage_elems = (long long)(ncol + 1) * TR;
-  T* const smem0 = reinterpret_cast<T*>(tma_smem);
-  if (tid == 0) {
-    for (int i = 0; i < kTmaStages; ++i) mbar_init(&bar[i], 1);
-    fence_mbar_init();
-    s_abort = 0;
-  }
   pdl_wait();   // w, Q and h come from earlier kernels
   if (KIND != kGemvT) {
-    for (int j = tid; j < ncol; j += kRedThreads) {
+    for (int j = threadIdx.x; j < ncol; j += kRedThreads) {
       sh1[j] = (T)h1[j];
       if (KIND == kFinal) sh2[j] = (T)h2[j];
     }
+    __syncthreads();
   }
-  __syncthreads();
-  // warp 0: bring tile t into stage sidx.  Lane 0 posts the expected bytes;
-  // the lanes issue the ncol+1 copies in parallel (a copy may land before
-  // the expectation is posted: the transaction count goes negative meanwhile).
-  auto issue = [&](long long t, int sidx) {
-    if (t >= ntiles) return;
-    const long long r0 = t * TR;
-    const long long rows = ns - r0 < TR ? ns - r0 : TR;
-    const unsigned bytes = (unsigned)(rows * sizeof(T));
-    T* const dst = smem0 + sidx * stage_elems;
-    unsigned long long* const b = &bar[sidx];
-    const int lane = tid & 31;
-    if (lane == 0) mbar_expect_tx(b, bytes * (unsigned)(ncol + 1));
-    for (int v = lane; v <= ncol; v += 32) {
-      const T* src = v == 0 ? w + r0 : Q + (v - 1) * ns + r0;
-      bulk_g2s(dst + (long long)v * TR, src, bytes, b);
-    }
-  };
-  if (tid < 32)
-    for (int i = 0; i < kTmaStages; ++i) issue(blockIdx.x + (long long)i * gridDim.x, i);
   T acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = T(0);
-  unsigned phases = 0u;   // bit i: parity of stage i
-  int sidx = 0;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const bool ok = mbar_wait(&bar[sidx], (phases >> sidx) & 1u);
-    if (!ok) s_abort = 1;
-    phases ^= 1u << sidx;
-    const T* st = smem0 + sidx * stage_elems;
-    const int rows = (int)(ns - t * TR < TR ? ns - t * TR : TR);
-    if (ok) {
-      for (int r = tid; r < rows; r += kRedThreads) {
-        T wr = st[r];
-        if (KIND == kGemvT) {
+  const long long ng = ns / V;
+  const long long stride = (long long)gridDim.x * kRedThreads;
+  for (long long g = blockIdx.x * (long long)kRedThreads + threadIdx.x; g < ng; g += stride) {
+    const long long r0 = g * V;
+    T wr[V];
+    ld_group<T, V>(w + r0, wr);
+    T q[KMAX][V];
 #pragma unroll
-          for (int j = 0; j < KMAX; ++j)
-            if (j < ncol) acc[j] = fma(st[(j + 1) * TR + r], wr, acc[j]);
-        } else if (KIND == kReorth) {
-          T s1 = T(0);
+    for (int j = 0; j < KMAX; ++j)
+      if (j < ncol) ld_group<T, V>(Q + j * ns + r0, q[j]);
+    if (KIND == kGemvT) {
 #pragma unroll
-          for (int j = 0; j < KMAX; ++j)
-            if (j < ncol) s1 = fma(st[(j + 1) * TR + r], sh1[j], s1);
-          wr = wr - s1;   // w - Q h1
+      for (int j = 0; j < KMAX; ++j)
+        if (j < ncol) {
 #pragma unroll
-          for (int j = 0; j < KMAX; ++j)
-            if (j < ncol) acc[j] = fma(st[(j + 1) * TR + r], wr, acc[j]);
-        } else {
-          T s1 = T(0), s2 = T(0);
-#pragma unroll
-          for (int j = 0; j < KMAX; ++j)
-            if (j < ncol) {
-              const T q = st[(j + 1) * TR + r];
-              s1 = fma(q, sh1[j], s1);
-              s2 = fma(q, sh2[j], s2);
-            }
-          wr = (wr - s1) - s2;   // (w - Q h1) - Q h2
-          qnew[t * TR + r] = wr;
-          acc[0] = fma(wr, wr, acc[0]);
+          for (int v = 0; v < V; ++v) acc[j] = fma(q[j][v], wr[v], acc[j]);
         }
+    } else if (KIND == kReorth) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T s1 = T(0);
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+          if (j < ncol) s1 = fma(q[j][v], sh1[j], s1);
+        wr[v] = wr[v] - s1;   // w - Q h1
       }
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j)
+        if (j < ncol) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[j] = fma(q[j][v], wr[v], acc[j]);
+        }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T s1 = T(0), s2 = T(0);
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+          if (j < ncol) {
+            s1 = fma(q[j][v], sh1[j], s1);
+            s2 = fma(q[j][v], sh2[j], s2);
+          }
+        wr[v] = (wr[v] - s1) - s2;   // (w - Q h1) - Q h2
+        acc[0] = fma(wr[v], wr[v], acc[0]);
+      }
+      st_group<T, V>(qnew + r0, wr);
     }
-    __syncthreads();   // every thread is done with this stage (and s_abort is seen)
-    if (s_abort) break;
-    if (tid < 32) {
-      fence_proxy_async_smem();
-      issue(t + (long long)kTmaStages * gridDim.x, sidx);
-    }
-    sidx = sidx + 1 == kTmaStages ? 0 : sidx + 1;
   }
-  if (s_abort) {
-    // a copy never completed: flag it, give the copies in flight a bounded
-    // chance to land before the CTA's shared memory goes away
-    if (tid == 0) {
-      atomicExch(err, 1);
-      for (int i = 0; i < kTmaStages; ++i) mbar_wait(&bar[i], (phases >> i) & 1u);
-    }
-    __syncthreads();
+  const int nred = KIND == kFinal ? 1 : ncol;
+  if (!block_partials_last<T, KMAX>(acc, nred, partials, counter, sums)) return;
+  if (KIND != kFinal) {
+    for (int j = threadIdx.x; j < nred; j += kRedThreads) out[j] = sums[j];
+  } else if (threadIdx.x < 32) {
+    arnoldi_givens_warp<KMAX>(sqrt(sums[0]), ncol - 1, h1, h2, H, ldh, cs, sn, t, st, next);
   }
-  reduce_publish<T, KMAX>(acc, KIND == kFinal ? 1 : ncol, partials, counter, out);
 }
 
-// beta = ||q_new||, q_new /= beta, and (block 0) the Arnoldi column
-// H[:,k] = h1 + h2, H[k+1,k] = beta followed by the Givens update of
-// Algorithm 3: rotations 0..k-1 applied to column k, rotation k formed to
-// zero H[k+1,k], t updated, rho = |t[k+1]|.  In graph mode the kernel opens
-// the next step's IF node (handle `next`) while the cycle stays active.
+// q_new /= beta (the Arnoldi normalisation), beta from the solve state.
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
-arnoldi_finish_kernel(T* __restrict__ qnew, long long ns, const double* __restrict__ partials,
-                      int nparts, int k, const double* __restrict__ h1,
-                      const double* __restrict__ h2, double* __restrict__ H, int ldh,
-                      double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ t,
-                      SolveState* st, unsigned long long next) {
+__global__ void __launch_bounds__(256)
+arnoldi_scale_kernel(T* __restrict__ qnew, long long ns, const SolveState* st) {
   pdl_trigger();
   pdl_wait();
-  __shared__ double red[kRedThreads];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nparts; b += kRedThreads) s += partials[(long long)b * kPartStride];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double beta = sqrt(red[0]);
-  const bool finite = isfinite(beta);
-  if (finite && beta > 0.0) {
-    const T inv = (T)(1.0 / beta);
-    const long long stride = (long long)gridDim.x * kRedThreads;
-    for (long long g = blockIdx.x * (long long)kRedThreads + threadIdx.x; g < (ns >> 2);
-         g += stride) {
-      T v[4];
-      Vec4<T>::ld_cs(qnew + (g << 2), v);
+  const double beta = st->beta;
+  if (!(isfinite(beta) && beta > 0.0)) return;
+  const T inv = (T)(1.0 / beta);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (ns >> 2);
+       g += stride) {
+    T v[4];
+    Vec4<T>::ld_cs(qnew + (g << 2), v);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) v[r] = v[r] * inv;
-      Vec4<T>::st(qnew + (g << 2), v);
-    }
+    for (int r = 0; r < 4; ++r) v[r] = v[r] * inv;
+    Vec4<T>::st(qnew + (g << 2), v);
   }
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double* hc = H + (long long)k * ldh;
-  for (int j = 0; j <= k; ++j) hc[j] = h1[j] + h2[j];
-  hc[k + 1] = beta;
-  st->beta = beta;
-  bool go = false;
-  if (!finite) {
-    st->status = HPG_ERR_NAN;
-    st->active = 0;
-  } else {
-    for (int j = 0; j < k; ++j) {
-      const double a = hc[j], b = hc[j + 1];
-      hc[j] = cs[j] * a + sn[j] * b;
-      hc[j + 1] = -sn[j] * a + cs[j] * b;
-    }
-    const double mu = hypot(hc[k], hc[k + 1]);
-    if (!(mu > 0.0) || !isfinite(mu)) {
-      st->status = isfinite(mu) ? HPG_ERR_BREAKDOWN : HPG_ERR_NAN;
-      st->active = 0;
-    } else {
-      cs[k] = hc[k] / mu;
-      sn[k] = hc[k + 1] / mu;
-      hc[k] = mu;
-      hc[k + 1] = 0.0;
-      t[k + 1] = -sn[k] * t[k];
-      t[k] = cs[k] * t[k];
-      const double rho = fabs(t[k + 1]);
-      st->rho = rho;
-      st->k = k + 1;
-      st->iters += 1;
-      go = !(rho / st->rho0 < st->tol || st->iters >= st->maxit || k + 1 >= st->m);
-      st->active = go ? 1 : 0;
-    }
-  }
-  if (next) cudaGraphSetConditional(next, go ? 1u : 0u);
 }
 
 // y = H[:k,:k]^{-1} t[:k] (the dense TRSM of Algorithm 3), one warp,
@@ -518,8 +512,8 @@ update_x_kernel(double* __restrict__ x, const T* __restrict__ d, long long ns) {
   if (i < ns) x[i] += (double)d[i];
 }
 
-// r = b - A x and ||r||^2 (FP64), reduced through the cluster tree.
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kRedThreads)
+// r = b - A x and ||r||^2 (FP64).
+__global__ void __launch_bounds__(kRedThreads)
 residual_norm_kernel(const double* __restrict__ vals, const int* __restrict__ cols, long long ns,
                      const double* __restrict__ b, const double* __restrict__ x,
                      double* __restrict__ r, double* __restrict__ partials,
@@ -540,11 +534,13 @@ residual_norm_kernel(const double* __restrict__ vals, const int* __restrict__ co
     r[row] = v;
     acc[0] = fma(v, v, acc[0]);
   }
-  reduce_publish<double, 1>(acc, 1, partials, counter, out);
+  __shared__ double sums[1];
+  if (block_partials_last<double, 1>(acc, 1, partials, counter, sums) && threadIdx.x == 0)
+    out[0] = sums[0];
 }
 
 // ||v||^2 of an FP64 vector.
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads)
 norm2_kernel(const double* __restrict__ v, long long ns, double* __restrict__ partials,
              unsigned int* counter, double* __restrict__ out) {
   pdl_trigger();
@@ -553,7 +549,9 @@ norm2_kernel(const double* __restrict__ v, long long ns, double* __restrict__ pa
   const long long stride = (long long)gridDim.x * kRedThreads;
   for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < ns; i += stride)
     acc[0] = fma(v[i], v[i], acc[0]);
-  reduce_publish<double, 1>(acc, 1, partials, counter, out);
+  __shared__ double sums[1];
+  if (block_partials_last<double, 1>(acc, 1, partials, counter, sums) && threadIdx.x == 0)
+    out[0] = sums[0];
 }
 
 // Outer convergence test of Algorithm 3 on the FP64 residual norm:
@@ -621,100 +619,47 @@ __global__ void delay_kernel(long long cycles) {
 // ----------------------------------------------------------------- launchers
 template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? HPG_FP64 : HPG_FP32; }
 
-// Tile rows: kTmaStages stages of (w + ncol columns) x TR in the shared memory a
-// CTA may use without opting in (48 KB) minus the kernel's static shared
-// memory; TR a multiple of 32 in [32, 2048] (16-byte aligned copies and
-// sizes).
-constexpr long long kTmaSmemBytes = HPG_TMA_SMEM_KB * 1024LL;   // opted-in shared memory per CTA
-
-template <typename T>
-static int tma_rows(int ncol, size_t static_smem) {
-  const long long per_row = (long long)kTmaStages * (ncol + 1) * sizeof(T);
-  const long long budget = kTmaSmemBytes - (long long)static_smem - 256;
-  long long tr = budget / per_row / 32 * 32;
-  if (tr < 32) tr = 32;
-  if (tr > 2048) tr = 2048;
-  return (int)tr;
-}
-
-// Static shared memory of an instantiation; also opts it into
-// kTmaSmemBytes of shared memory per CTA (once per process and device).
+// Grid of a CGS2 pass: every resident block of the instantiation (one wave
+// of grid-stride blocks), at most the G blocks the partials are sized for.
 template <typename T, int KMAX, int KIND>
-static size_t tma_static_smem() {
-  static size_t bytes = 0;
-  if (bytes == 0) {
-    cudaFuncAttributes a;
-    bytes = cudaFuncGetAttributes(&a, cgs2_tma_kernel<T, KMAX, KIND>) == cudaSuccess
-                ? a.sharedSizeBytes
-                : 16384;
-    cudaFuncSetAttribute(cgs2_tma_kernel<T, KMAX, KIND>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kTmaSmemBytes - (long long)bytes));
-    cudaGetLastError();
+static int pass_grid(hpg_problem* h) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs2_pass_kernel<T, KMAX, KIND>,
+                                                      kRedThreads, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
   }
-  return bytes;
-}
-
-// Grid of a TMA pass: as many whole clusters as can be resident at once.
-template <typename T, int KMAX, int KIND>
-static int tma_grid(hpg_problem* h, size_t smem) {
-  auto kern = cgs2_tma_kernel<T, KMAX, KIND>;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kCluster);
-  cfg.blockDim = dim3(kRedThreads);
-  cfg.dynamicSmemBytes = smem;
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
-    cudaGetLastError();
-    nclusters = h->num_sms / kCluster;
-  }
-  const int cap = h->ws->G;   // partials are sized for this many CTAs
-  int g = nclusters * kCluster;
-  return g < cap ? g : cap;
+  const int g = per_sm * h->num_sms;
+  return g < h->ws->G ? g : h->ws->G;
 }
 
 template <typename T, int KMAX, int KIND>
-static cudaError_t enqueue_tma(hpg_problem* h, const T* Q, long long ns, int ncol, const T* w,
-                               T* qnew, double* out, cudaStream_t s, int* grid_out) {
+static cudaError_t enqueue_pass(hpg_problem* h, const T* Q, long long ns, int ncol, const T* w,
+                                T* qnew, double* out, int k, unsigned long long next,
+                                cudaStream_t s) {
   Workspace* ws = h->ws;
-  const size_t ssmem = tma_static_smem<T, KMAX, KIND>();
-  const int tr = tma_rows<T>(ncol, ssmem);
-  const size_t smem = (size_t)kTmaStages * (ncol + 1) * tr * sizeof(T);
-  if ((long long)(smem + ssmem) > kTmaSmemBytes) {
-    // cannot happen for k + 1 <= 64 columns: the 32-row floor needs 50 KB at most
-    set_error("cgs2: %zu + %zu bytes of shared memory exceed %lld", smem, ssmem, kTmaSmemBytes);
-    return cudaErrorInvalidConfiguration;
-  }
-  const int grid = tma_grid<T, KMAX, KIND>(h, smem);
-  *grid_out = grid;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kRedThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  if (h->pdl_enabled && h->pdl_next && !h->profiling) {
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-  }
-  return cudaLaunchKernelEx(&cfg, cgs2_tma_kernel<T, KMAX, KIND>, Q, ns, ncol, w,
-                            (const double*)ws->h1, (const double*)ws->h2, qnew, tr,
-                            ws->partials, ws->counter, out, ws->dev_err);
+  return kl(h, cgs2_pass_kernel<T, KMAX, KIND>, pass_grid<T, KMAX, KIND>(h), kRedThreads, s, Q,
+            ns, ncol, w, (const double*)ws->h1, (const double*)ws->h2, qnew, ws->partials,
+            ws->counter, out, ws->H, ws->m + 1, ws->cs, ws->sn, ws->t, ws->st, next);
 }
 
+// One CGS2 pass over q_0..q_{ncol-1} (k = ncol - 1); the final pass also
+// forms the Arnoldi column and the Givens update and opens `next`.
 template <typename T, int KIND>
 static int launch_pass(hpg_problem* h, const T* Q, long long ns, int ncol, const T* w, T* qnew,
-                       double* out, cudaStream_t s, int* grid_out) {
+                       double* out, unsigned long long next, cudaStream_t s) {
   static const int cls[3] = {K_CGS2_GEMVT, K_CGS2_REORTH, K_CGS2_FINAL};
   const double vecs = ncol + (KIND == kFinal ? 2 : 1);   // Q columns + w (+ q_new)
   const double bytes = (double)h->lev[0].n * vecs * sizeof(T);
-  return launch(h, cls[KIND], 0, prec_of<T>(), bytes, s, "cgs2_tma_kernel", [&] {
-    if (ncol <= 8) return enqueue_tma<T, 8, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
-    if (ncol <= 16) return enqueue_tma<T, 16, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
-    if (ncol <= 32) return enqueue_tma<T, 32, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
-    return enqueue_tma<T, 64, KIND>(h, Q, ns, ncol, w, qnew, out, s, grid_out);
+  const int k = ncol - 1;
+  return launch(h, cls[KIND], 0, prec_of<T>(), bytes, s, "cgs2_pass_kernel", [&] {
+    if (ncol <= 8) return enqueue_pass<T, 8, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
+    if (ncol <= 16) return enqueue_pass<T, 16, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
+    if (ncol <= 32) return enqueue_pass<T, 32, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
+    return enqueue_pass<T, 64, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
   });
 }
 
@@ -733,16 +678,13 @@ static int enqueue_step(hpg_problem* h, int k, hpg_prec prec, unsigned long long
   if ((rc = launch_spmv(h, 0, prec, z, w, s))) return rc;
   const int ncol = k + 1;
   T* qnew = Q + (long long)(k + 1) * ns;
-  int g_final = 0;
-  if ((rc = launch_pass<T, kGemvT>(h, Q, ns, ncol, w, nullptr, ws->h1, s, &g_final))) return rc;
-  if ((rc = launch_pass<T, kReorth>(h, Q, ns, ncol, w, nullptr, ws->h2, s, &g_final))) return rc;
-  if ((rc = launch_pass<T, kFinal>(h, Q, ns, ncol, w, qnew, nullptr, s, &g_final))) return rc;
-  return launch(h, K_ARNOLDI_FINISH, 0, prec_of<T>(), 2.0 * h->lev[0].n * sizeof(T), s,
-                "arnoldi_finish_kernel", [&] {
-                  return kl(h, arnoldi_finish_kernel<T>, ws->G, kRedThreads, s, qnew, ns,
-                            (const double*)ws->partials, g_final / kCluster, k,
-                            (const double*)ws->h1, (const double*)ws->h2, ws->H, ws->m + 1,
-                            ws->cs, ws->sn, ws->t, ws->st, next);
+  if ((rc = launch_pass<T, kGemvT>(h, Q, ns, ncol, w, nullptr, ws->h1, 0ULL, s))) return rc;
+  if ((rc = launch_pass<T, kReorth>(h, Q, ns, ncol, w, nullptr, ws->h2, 0ULL, s))) return rc;
+  if ((rc = launch_pass<T, kFinal>(h, Q, ns, ncol, w, qnew, nullptr, next, s))) return rc;
+  return launch(h, K_ARNOLDI_SCALE, 0, prec_of<T>(), 2.0 * h->lev[0].n * sizeof(T), s,
+                "arnoldi_scale_kernel", [&] {
+                  return kl(h, arnoldi_scale_kernel<T>, grid_for(ns / 4, 256), 256, s, qnew, ns,
+                            (const SolveState*)ws->st);
                 });
 }
 

@@ -29,8 +29,8 @@ struct Profiler {
 
 static const char* kNames[K_NUM_CLASSES] = {
     "gen_ell",      "permute",         "spmv",        "residual_fp64", "gs_colour_phase",
-    "restrict",     "prolong",         "cgs2_gemvt",  "cgs2_reorth",   "cgs2_final_norm",
-    "arnoldi_finish_givens", "trsm",   "basis_combine", "update_x",    "cycle_start",
+    "restrict",     "prolong",         "cgs2_gemvt",  "cgs2_reorth",   "cgs2_final_givens",
+    "arnoldi_scale", "trsm",           "basis_combine", "update_x",    "cycle_start",
     "norm",         "vcycle_coarse_cluster"};
 
 const char* kernel_class_name(int cls) {

@@ -330,6 +330,26 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   return HPG_OK;
 }
 
+// `sweeps` symmetric sweeps on one level; from_zero: z enters as 0 (its
+// contents are never read).
+template <typename T>
+static int smooth_t(hpg_problem* h, int level, const T* r, T* z, int sweeps, bool from_zero,
+                    cudaStream_t s) {
+  const Level& L = h->lev[level];
+  if (sweeps == 0) {
+    if (from_zero) {
+      HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
+      h->pdl_next = false;
+    }
+    return HPG_OK;
+  }
+  SweepState st;
+  int rc;
+  for (int it = 0; it < sweeps; ++it)
+    if ((rc = symgs<T>(h, level, r, z, from_zero && it == 0, st, s))) return rc;
+  return HPG_OK;
+}
+
 int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
                cudaStream_t s) {
   if (prec == HPG_FP64) return vcycle_t<double>(h, level, (const double*)r, (double*)z, s);
@@ -368,6 +388,25 @@ HPG_API int hpg_mg_vcycle(hpg_problem_t* h, int level, hpg_prec prec, const void
   }
   h->pdl_next = false;
   return run_vcycle(h, level, prec, r, z, (cudaStream_t)stream);
+}
+
+HPG_API int hpg_mg_smooth(hpg_problem_t* h, int level, hpg_prec prec, const void* r, void* z,
+                          int sweeps, int z_is_zero, void* stream) {
+  if (!h || !r || !z || level < 0 || level >= h->nlev ||
+      (prec != HPG_FP64 && prec != HPG_FP32) || r == z || sweeps < 0) {
+    set_error("hpg_mg_smooth: invalid argument (handle, level %d, prec %d, sweeps %d, pointers)",
+              level, (int)prec, sweeps);
+    return HPG_ERR_INVALID;
+  }
+  if (!h->hierarchy) {
+    set_error("hpg_mg_smooth: call hpg_build_mg_hierarchy first");
+    return HPG_ERR_STATE;
+  }
+  h->pdl_next = false;
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (prec == HPG_FP64)
+    return smooth_t<double>(h, level, (const double*)r, (double*)z, sweeps, z_is_zero != 0, s);
+  return smooth_t<float>(h, level, (const float*)r, (float*)z, sweeps, z_is_zero != 0, s);
 }
 
 }  // extern "C"

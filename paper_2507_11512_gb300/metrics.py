@@ -89,13 +89,20 @@ def penalty(n_d, n_ir):
     return min(1.0, n_d / n_ir)
 
 
+def gs_row_bytes(value_bytes, vector_bytes):
+    """Algorithmic DRAM bytes of one row of a Gauss-Seidel colour phase: the
+    27 ELL values, the 26 off-diagonal int32 indices, r_i, the write of z_i and
+    the gathered z_j (each neighbour value read once over the sweep)."""
+    return 27 * value_bytes + 26 * 4 + 3 * vector_bytes
+
+
 def inner_iteration_bytes(dims_list, k, value_bytes, vector_bytes, pre=1, post=1):
     """Algorithmic DRAM bytes of one inner step at basis size k+1 (context)."""
     sv, sx = value_bytes, vector_bytes
     tot = 0.0
     for lev, d in enumerate(dims_list):
         n = d[0] * d[1] * d[2]
-        gs_row = 27 * sv + 26 * 4 + 3 * sx
+        gs_row = gs_row_bytes(sv, sx)
         sweeps = 1 if lev == len(dims_list) - 1 else pre + post
         tot += sweeps * 15 / 8 * n * gs_row
         if lev < len(dims_list) - 1:

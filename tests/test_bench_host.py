@@ -83,3 +83,14 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "GFLOP/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
+
+
+def test_gs_traffic_only_for_unchanged_kernel_sources(monkeypatch):
+    import bench
+    monkeypatch.setitem(bench.GS_TRAFFIC, "bytes_per_launch", 1.0e6)
+    monkeypatch.setitem(bench.GS_TRAFFIC, "sources_sha256", "0" * 64)
+    assert bench.gs_traffic() is None
+    monkeypatch.setitem(bench.GS_TRAFFIC, "sources_sha256", bench.gs_sources_sha256())
+    assert bench.gs_traffic() == 1.0e6
+    monkeypatch.setitem(bench.GS_TRAFFIC, "bytes_per_launch", None)
+    assert bench.gs_traffic() is None

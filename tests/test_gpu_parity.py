@@ -282,7 +282,7 @@ def test_graph_and_eager_paths_agree(inner):
     assert iq["graph_launches"] == 0 and iq["kernel_launches"] == ig["kernel_launches"]
     names = {r["name"] for r in rep}
     assert {"gs_colour_phase", "restrict", "prolong", "spmv", "cgs2_gemvt", "cgs2_reorth",
-            "cgs2_final_norm", "arnoldi_finish_givens", "residual_fp64"} <= names
+            "cgs2_final_givens", "arnoldi_scale", "residual_fp64"} <= names
     # with the coarse-level cluster kernel the whole (small) V-cycle is one kernel
     with hpg.Problem(*dims, beta=beta) as p:
         hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CLUSTER, 1)

@@ -61,6 +61,7 @@ def test_host_side_validation_without_gpu(lib):
         _lib.HPG_ERR_INVALID
     assert lib.hpg_spmv(None, 0, 1, None, None, None) == _lib.HPG_ERR_INVALID
     assert lib.hpg_mg_vcycle(None, 0, 1, None, None, None) == _lib.HPG_ERR_INVALID
+    assert lib.hpg_mg_smooth(None, 0, 1, None, None, 1, 1, None) == _lib.HPG_ERR_INVALID
     assert lib.hpg_build_mg_hierarchy(None, 4, 1, 1) == _lib.HPG_ERR_INVALID
     assert lib.hpg_destroy(None) == _lib.HPG_OK
     cnt = ctypes.c_int()

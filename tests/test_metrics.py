@@ -45,3 +45,9 @@ def test_fullscale_table_ratios_are_consistent():
     rows = json.load(open(GOLDEN))["fullscale_table"]["rows"]
     for r in rows:
         assert metrics.penalty(r["fullscale_ratio"], 1.0) == min(1.0, r["fullscale_ratio"])
+
+
+def test_gs_row_bytes_fp32_and_fp64():
+    # 27 values + 26 int32 indices + r_i, z_i written, z_j gathered
+    assert metrics.gs_row_bytes(4, 4) == 27 * 4 + 26 * 4 + 12 == 224
+    assert metrics.gs_row_bytes(8, 8) == 27 * 8 + 26 * 4 + 24 == 344
