@@ -34,7 +34,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the level-0 FP32 Gauss-Seidel phase
 # kernel at 128^3, from one ncu capture (profiles/gs_phase_level0_128cube.md),
 # valid while the kernel sources hash to `sources_sha256`.
-GS_TRAFFIC = {"bytes_per_launch": 65346048.0,
+GS_TRAFFIC = {"workload": "mxp_gmres30_128cube", "bytes_per_launch": 65346048.0,
               "sources_sha256": "54d71c2ac4eb47e887c92c558329833224c2f8152e9840df9cb2a445b64a9798"}
 GS_SOURCES = ("paper_2507_11512_gb300/csrc/sparse.cu", "paper_2507_11512_gb300/csrc/hpg_internal.cuh")
 
@@ -48,9 +48,10 @@ def gs_sources_sha256():
     return h.hexdigest()
 
 
-def gs_traffic():
-    """Captured DRAM traffic per launch, or None if the kernel changed since."""
-    if GS_TRAFFIC["bytes_per_launch"] is None:
+def gs_traffic(workload="mxp_gmres30_128cube"):
+    """Captured DRAM traffic per launch, or None if the kernel changed since
+    (or the capture was of another workload)."""
+    if GS_TRAFFIC["bytes_per_launch"] is None or workload != GS_TRAFFIC["workload"]:
         return None
     return GS_TRAFFIC["bytes_per_launch"] if gs_sources_sha256() == GS_TRAFFIC[
         "sources_sha256"] else None
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="mxp_gmres30_128cube")
+    ap.add_argument("--basis", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="storage of the Krylov basis in the mixed-precision solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=8)
@@ -238,10 +241,13 @@ def run_gpu(args):
     b = ax + torch.tensor(rhs_noise(n, w.noise_std, w.seed), device=dev)
     x = torch.zeros_like(b)
 
+    basis_mxp = {"fp32": hpg.HPG_FP32, "bf16": hpg.HPG_BF16, "fp16": hpg.HPG_FP16}[args.basis]
+
     def solve(inner):
         x.zero_()
         return hpg.gmres_ir_solve(prob.h, b, x, tol=w.tol, restart=w.restart, maxit=w.maxit,
-                                  inner=inner)
+                                  inner=inner,
+                                  basis=basis_mxp if inner == hpg.HPG_FP32 else inner)
 
     def timed(inner, steps, warmup):
         for _ in range(warmup):
@@ -330,7 +336,7 @@ def run_gpu(args):
     gs_phases = 15
     gs_bytes = (sum(cnt) + sum(cnt[:7])) * gs_row_bytes * gs_reps
     gs_gbs = gs_bytes / (gs_ms / 1e3) / 1e9
-    traffic = gs_traffic()
+    traffic = gs_traffic(w.name)
     roofline = {"bound": "hbm", "kernel": "gs_phase_kernel (level 0, fp32)",
                 "achieved": gs_gbs, "peak": peak, "unit": "GB/s", "frac": gs_gbs / peak,
                 "peak_source": peak_src,
@@ -352,14 +358,14 @@ def run_gpu(args):
     for _ in range(1):
         xh.zero_()
         hpg.gmres_ir_solve(prob.h, bh, xh, tol=w.tol, restart=w.restart, maxit=w.maxit,
-                           inner=hpg.HPG_FP32)
+                           inner=hpg.HPG_FP32, basis=basis_mxp)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_fl = 0
     for _ in range(args.steps):
         xh.zero_()
         inf = hpg.gmres_ir_solve(prob.h, bh, xh, tol=w.tol, restart=w.restart, maxit=w.maxit,
-                                 inner=hpg.HPG_FP32)
+                                 inner=hpg.HPG_FP32, basis=basis_mxp)
         e2e_fl += metrics.solve_flops(dims_list, metrics.cycles_from_info(
             inf["iterations"], inf["restarts"], w.restart))
     torch.cuda.synchronize()
@@ -385,7 +391,7 @@ def run_gpu(args):
                        "restart": w.restart, "tol": w.tol, "levels": len(dims_list),
                        "smoother": "1+1 symmetric multicolour Gauss-Seidel",
                        "rhs": "A*1 + N(0, %g^2), seed %d" % (w.noise_std, w.seed),
-                       "inner": "fp32", "outer": "fp64",
+                       "inner": "fp32", "basis": args.basis, "outer": "fp64",
                        "l2": "inputs larger than L2 (FP32 ELL matrix %.0f MB)" % (
                            prob.n_store() * 27 * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -207,10 +207,16 @@ HPG_API int hpg_mg_vcycle_noalloc(hpg_problem_t* h, int level, hpg_prec prec,
  * CGS2 and Givens rotations.  The outer residual r = b - A x, its norm, the
  * convergence test ||r||/||b|| < tol, the update x += M^{-1} Q t and the
  * Hessenberg least-squares run in FP64; `inner` (HPG_FP32 or HPG_FP64) is the
- * precision of the V-cycle and the Arnoldi SpMV; `basis` (HPG_FP64, HPG_FP32,
- * HPG_BF16, HPG_FP16) the storage of the Krylov basis Q (BF16/FP16 need
- * inner = HPG_FP32).  inner = basis = HPG_FP64 is plain FP64 GMRES
- * (Algorithm 2).  b: FP64, natural order, n entries; x: FP64, natural order,
+ * precision of the V-cycle and the Arnoldi SpMV; `basis` the storage of the
+ * Krylov basis Q: HPG_FP64 with inner = HPG_FP64 (plain FP64 GMRES,
+ * Algorithm 2), or with inner = HPG_FP32 one of HPG_FP32, HPG_BF16, HPG_FP16.
+ * A BF16/FP16 basis (the low-precision basis of Sec. 6's outlook) stores each
+ * vector as u_j = q_j / max_i |q_ij| with one FP32 scale sigma_j =
+ * max_i |q_ij| (so q_j = sigma_j u_j, |u_j| <= 1: no overflow, no vector
+ * flushed to zero); CGS2 reads it with FP32 arithmetic, the V-cycle is
+ * applied to the dequantised vector, and the FP64 refinement recovers the
+ * accuracy the basis loses (more inner steps may be needed).  Other
+ * combinations return HPG_ERR_UNSUPPORTED.  b: FP64, natural order, n entries; x: FP64, natural order,
  * in: initial guess, out: solution.  b and x may be device or host pointers
  * (host buffers are staged through device memory).  restart in [1, 64],
  * maxit >= 0 (total inner steps), tol > 0.  Returns HPG_OK on convergence,

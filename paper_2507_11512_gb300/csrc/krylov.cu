@@ -8,6 +8,8 @@
 // per-thread accumulation in T; block and global sums, H, the rotations, t, y,
 // the outer residual, its norm and x are FP64.
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
 
@@ -37,13 +39,17 @@ struct SolveState {
   int done;       // outer loop finished
   int converged;  // ||b - A x|| / ||b|| < tol
   double rel;     // latest true relative residual (FP64)
+  double wmax;    // max |w''| of the latest Arnoldi vector (scaled bases)
 };
 
 struct Workspace {
   int m = 0;              // restart capacity
-  hpg_prec prec = HPG_FP32;
+  hpg_prec prec = HPG_FP32;   // inner precision T
+  hpg_prec basis = HPG_FP32;  // basis storage B
   int G = 0;              // blocks of the reduction kernels
-  void* Q = nullptr;      // [m+1][ns] basis
+  void* Q = nullptr;      // [m+1][ns] basis (B)
+  float* qscale = nullptr;  // [m+1] per-vector scales of a 2-byte basis
+  float* qf = nullptr;    // [ns] current basis vector, dequantised (2-byte basis)
   void* z = nullptr;      // [ns] M^{-1} q_k, then M^{-1} (Q y)
   void* w = nullptr;      // [ns] A z
   void* u = nullptr;      // [ns] Q y
@@ -60,7 +66,7 @@ struct Workspace {
   double* sn = nullptr;
   double* t = nullptr;
   double* y = nullptr;
-  double* rho2 = nullptr;  // ||r||^2 of the outer residual
+  double* rho2 = nullptr;  // ||r||^2 and max |r| of the outer residual
   int* dev_err = nullptr;  // set by a kernel whose bounded wait gave up
   SolveState* st = nullptr;      // device
   SolveState* st_host = nullptr; // pinned mirror
@@ -70,6 +76,7 @@ struct Workspace {
   cudaGraphExec_t exec = nullptr;
   int graph_m = 0;
   hpg_prec graph_prec = HPG_FP32;
+  hpg_prec graph_basis = HPG_FP32;
   int graph_nodes = 0;
   // kernels per segment of the captured graph (for the launch count)
   long long n_outer = 0, n_start = 0, n_step = 0, n_update = 0;
@@ -85,15 +92,16 @@ void destroy_workspace(hpg_problem* h) {
     if (ws->cap[i]) cudaStreamDestroy(ws->cap[i]);
   void* ptrs[] = {ws->Q,  ws->z,  ws->w,  ws->u,  ws->b,  ws->x,    ws->r,
                   ws->stage, ws->partials, ws->counter, ws->h1, ws->h2, ws->H, ws->cs,
-                  ws->sn, ws->t,  ws->y,  ws->rho2, ws->st, ws->hk, ws->dev_err};
+                  ws->sn, ws->t,  ws->y,  ws->rho2, ws->st, ws->hk, ws->dev_err,
+                  ws->qscale, ws->qf};
   for (void* p : ptrs) dev_free(p);
   if (ws->st_host) cudaFreeHost(ws->st_host);
   delete ws;
   h->ws = nullptr;
 }
 
-static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec) {
-  if (h->ws && h->ws->m >= m && h->ws->prec == prec) return HPG_OK;
+static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec, hpg_prec basis) {
+  if (h->ws && h->ws->m >= m && h->ws->prec == prec && h->ws->basis == basis) return HPG_OK;
   destroy_workspace(h);
   Workspace* ws = new Workspace();
   h->ws = ws;
@@ -102,6 +110,7 @@ static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec) {
   const size_t es = prec_size(prec);
   ws->m = m;
   ws->prec = prec;
+  ws->basis = basis;
   // reduction grids: up to 8 blocks per SM (the CGS2 passes use one wave of
   // resident blocks, at most G)
   long long g = (ns + kRedThreads - 1) / kRedThreads;
@@ -109,7 +118,9 @@ static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec) {
   if (g > gmax) g = gmax;
   ws->G = (int)(g < 1 ? 1 : g);
   int rc = HPG_OK;
-  rc = rc ? rc : dev_alloc(&ws->Q, es * ns * (m + 1));
+  rc = rc ? rc : dev_alloc(&ws->Q, prec_size(basis) * ns * (m + 1));
+  rc = rc ? rc : dev_alloc((void**)&ws->qscale, sizeof(float) * (m + 1));
+  if (basis != prec) rc = rc ? rc : dev_alloc((void**)&ws->qf, sizeof(float) * ns);
   rc = rc ? rc : dev_alloc(&ws->z, es * ns);
   rc = rc ? rc : dev_alloc(&ws->w, es * ns);
   rc = rc ? rc : dev_alloc(&ws->u, es * ns);
@@ -147,6 +158,13 @@ template <typename A>
 __device__ __forceinline__ A warp_sum(A v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename A>
+__device__ __forceinline__ A warp_max(A v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -204,11 +222,35 @@ template <> struct Vec4<double> {
 // finish (atomic ticket) adds them in block order.
 enum PassKind { kGemvT = 0, kReorth = 1, kFinal = 2 };
 
+// ------------------------------------------------------------ basis storage
+// The Krylov basis is stored in the inner precision T, or -- FP32 inner solve
+// only -- in BF16 or FP16 with one FP32 scale per vector: q_j = sigma_j u_j
+// with u_j = q_j / max_i |q_ij| in [-1, 1], so FP16 can neither overflow nor
+// flush a whole vector to zero.  Arithmetic on the basis is in T.
+template <typename B>
+__host__ __device__ constexpr bool basis_scaled() {
+  return sizeof(B) == 2;
+}
+__device__ __forceinline__ float basis_to(float v) { return v; }
+__device__ __forceinline__ double basis_to(double v) { return v; }
+__device__ __forceinline__ float basis_to(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float basis_to(__half v) { return __half2float(v); }
+template <typename B> __device__ __forceinline__ B basis_from(float v);
+template <> __device__ __forceinline__ __nv_bfloat16 basis_from<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half basis_from<__half>(float v) {
+  return __float2half_rn(v);
+}
+
 // Rows per thread per iteration: the basis values of a row group (KMAX x V
-// elements) take at most 64 registers up to KMAX = 32 (FP32 and FP64).
-template <typename T, int KMAX>
+// elements of B) take at most 64 registers up to KMAX = 32 (FP64: 16), and
+// one row group of a column is one 16-, 8-, 4- or 2-byte load.
+template <typename B, int KMAX>
 __host__ __device__ constexpr int pass_vec() {
-  return sizeof(T) == 4 ? (KMAX <= 16 ? 4 : KMAX <= 32 ? 2 : 1) : (KMAX <= 8 ? 2 : 1);
+  return sizeof(B) == 8   ? (KMAX <= 8 ? 2 : 1)
+         : sizeof(B) == 4 ? (KMAX <= 16 ? 4 : KMAX <= 32 ? 2 : 1)
+                          : (KMAX <= 16 ? 8 : KMAX <= 32 ? 4 : 2);
 }
 // Resident blocks per SM the register budget is sized for.
 template <typename T, int KMAX>
@@ -216,37 +258,61 @@ __host__ __device__ constexpr int pass_min_blocks() {
   return (sizeof(T) == 4 ? KMAX <= 32 : KMAX <= 16) ? 2 : 1;
 }
 
-template <typename T, int V>
-__device__ __forceinline__ void ld_group(const T* p, T (&v)[V]) {
-  if constexpr (sizeof(T) * V == 16) {
-    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
-    memcpy(v, &t, 16);
-  } else if constexpr (sizeof(T) * V == 8) {
-    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+// V consecutive elements (V * sizeof(E) bytes, aligned to that size up to 16:
+// storage rows come in multiples of 32), streaming loads / plain stores.
+template <typename E, int V>
+__device__ __forceinline__ void ld_group(const E* p, E (&v)[V]) {
+  constexpr int bytes = (int)sizeof(E) * V;
+  if constexpr (bytes % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < bytes / 16; ++i) {
+      const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p) + i);
+      memcpy(reinterpret_cast<char*>(v) + 16 * i, &t, 16);
+    }
+  } else if constexpr (bytes == 8) {
+    const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
     memcpy(v, &t, 8);
+  } else if constexpr (bytes == 4) {
+    const unsigned t = __ldcs(reinterpret_cast<const unsigned*>(p));
+    memcpy(v, &t, 4);
   } else {
-    v[0] = __ldcs(p);
+    static_assert(bytes == 2, "row group of 2 to 16k bytes");
+    const unsigned short t = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    memcpy(v, &t, 2);
   }
 }
-template <typename T, int V>
-__device__ __forceinline__ void st_group(T* p, const T (&v)[V]) {
-  if constexpr (sizeof(T) * V == 16) {
-    float4 t;
-    memcpy(&t, v, 16);
-    *reinterpret_cast<float4*>(p) = t;
-  } else if constexpr (sizeof(T) * V == 8) {
-    float2 t;
+template <typename E, int V>
+__device__ __forceinline__ void st_group(E* p, const E (&v)[V]) {
+  constexpr int bytes = (int)sizeof(E) * V;
+  if constexpr (bytes % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < bytes / 16; ++i) {
+      uint4 t;
+      memcpy(&t, reinterpret_cast<const char*>(v) + 16 * i, 16);
+      reinterpret_cast<uint4*>(p)[i] = t;
+    }
+  } else if constexpr (bytes == 8) {
+    uint2 t;
     memcpy(&t, v, 8);
-    *reinterpret_cast<float2*>(p) = t;
+    *reinterpret_cast<uint2*>(p) = t;
+  } else if constexpr (bytes == 4) {
+    unsigned t;
+    memcpy(&t, v, 4);
+    *reinterpret_cast<unsigned*>(p) = t;
   } else {
-    *p = v[0];
+    static_assert(bytes == 2, "row group of 2 to 16k bytes");
+    unsigned short t;
+    memcpy(&t, v, 2);
+    *reinterpret_cast<unsigned short*>(p) = t;
   }
 }
 
 // Block sums of acc[0..nred) (FP64), stored as this block's partials; the last
 // block to arrive adds all blocks' partials in block order into sums[] (shared)
-// and returns true.  Every thread of the block must call it.
-template <typename A, int KMAX>
+// and returns true.  With MAXLAST the last entry is a maximum instead of a
+// sum (combined with max at every stage).  Every thread of the block must
+// call it.
+template <typename A, int KMAX, bool MAXLAST = false>
 __device__ bool block_partials_last(const A (&acc)[KMAX], int nred, double* __restrict__ partials,
                                     unsigned int* counter, double* sums) {
   __shared__ double red[kWarps][KMAX];
@@ -256,15 +322,17 @@ __device__ bool block_partials_last(const A (&acc)[KMAX], int nred, double* __re
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < nred) {
-      const A v = warp_sum(acc[j]);
+      const bool mx = MAXLAST && j == nred - 1;
+      const A v = mx ? warp_max(acc[j]) : warp_sum(acc[j]);
       if (lane == 0) red[warp][j] = (double)v;
     }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < nred; j += kRedThreads) {
+    const bool mx = MAXLAST && j == nred - 1;
     double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) s += red[q][j];
+    for (int q = 0; q < kWarps; ++q) s = mx ? fmax(s, red[q][j]) : s + red[q][j];
     partials[(long long)blockIdx.x * kPartStride + j] = s;
   }
   __threadfence();
@@ -275,17 +343,24 @@ __device__ bool block_partials_last(const A (&acc)[KMAX], int nred, double* __re
   __threadfence();
   constexpr int groups = kRedThreads / KMAX;
   const int j = threadIdx.x % KMAX, grp = threadIdx.x / KMAX;
+  const bool mx = MAXLAST && j == nred - 1;
   double s = 0.0;
   if (j < nred) {
 #pragma unroll 4
-    for (int b = grp; b < (int)gridDim.x; b += groups)
-      s += __ldcg(partials + (long long)b * kPartStride + j);
+    for (int b = grp; b < (int)gridDim.x; b += groups) {
+      const double v = __ldcg(partials + (long long)b * kPartStride + j);
+      s = mx ? fmax(s, v) : s + v;
+    }
   }
   red2[threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.x < nred) {
+    const bool mxj = MAXLAST && (int)threadIdx.x == nred - 1;
     double tsum = 0.0;
-    for (int q = 0; q < groups; ++q) tsum += red2[q * KMAX + threadIdx.x];
+    for (int q = 0; q < groups; ++q) {
+      const double v = red2[q * KMAX + threadIdx.x];
+      tsum = mxj ? fmax(tsum, v) : tsum + v;
+    }
     sums[threadIdx.x] = tsum;
   }
   if (threadIdx.x == 0) *counter = 0u;
@@ -356,23 +431,32 @@ __device__ void arnoldi_givens_warp(double beta, int k, const double* __restrict
   for (int j = lane; j <= k + 1; j += 32) hc[j] = hs[j];
 }
 
-template <typename T, int KMAX, int KIND>
+// One CGS2 pass (kind KIND) over the basis columns q_0..q_{ncol-1} stored as
+// B (scaled by qscale[j] when B is a 2-byte format: the scales are folded into
+// the coefficients and the results, so the inner loop only converts).  The
+// final pass writes w'' = (w - Q h1) - Q h2 to `wout` in T (a basis column
+// when B == T; w itself, in place, for a scaled basis, whose quantisation
+// needs max |w''| first) and reduces ||w''||^2 (and max |w''|).
+template <typename T, typename B, int KMAX, int KIND>
 __global__ void __launch_bounds__(kRedThreads, (pass_min_blocks<T, KMAX>()))
-cgs2_pass_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __restrict__ w,
-                 const double* __restrict__ h1, const double* __restrict__ h2,
-                 T* __restrict__ qnew, double* __restrict__ partials, unsigned int* counter,
-                 double* __restrict__ out, double* __restrict__ H, int ldh,
-                 double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ t,
-                 SolveState* st, unsigned long long next) {
-  constexpr int V = pass_vec<T, KMAX>();
+cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
+                 const float* __restrict__ qscale, const double* __restrict__ h1,
+                 const double* __restrict__ h2, T* wout, double* __restrict__ partials,
+                 unsigned int* counter, double* __restrict__ out, double* __restrict__ H,
+                 int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                 double* __restrict__ t, SolveState* st, unsigned long long next) {
+  constexpr int V = pass_vec<B, KMAX>();
+  constexpr bool S = basis_scaled<B>();
+  constexpr bool MAXLAST = S && KIND == kFinal;
   __shared__ T sh1[KMAX], sh2[KMAX];
   __shared__ double sums[KMAX];
   pdl_trigger();
   pdl_wait();   // w, Q and h come from earlier kernels
   if (KIND != kGemvT) {
     for (int j = threadIdx.x; j < ncol; j += kRedThreads) {
-      sh1[j] = (T)h1[j];
-      if (KIND == kFinal) sh2[j] = (T)h2[j];
+      const double sj = S ? (double)qscale[j] : 1.0;
+      sh1[j] = (T)(S ? h1[j] * sj : h1[j]);
+      if (KIND == kFinal) sh2[j] = (T)(S ? h2[j] * sj : h2[j]);
     }
     __syncthreads();
   }
@@ -385,16 +469,16 @@ cgs2_pass_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __res
     const long long r0 = g * V;
     T wr[V];
     ld_group<T, V>(w + r0, wr);
-    T q[KMAX][V];
+    B q[KMAX][V];
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-      if (j < ncol) ld_group<T, V>(Q + j * ns + r0, q[j]);
+      if (j < ncol) ld_group<B, V>(Q + j * ns + r0, q[j]);
     if (KIND == kGemvT) {
 #pragma unroll
       for (int j = 0; j < KMAX; ++j)
         if (j < ncol) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[j] = fma(q[j][v], wr[v], acc[j]);
+          for (int v = 0; v < V; ++v) acc[j] = fma((T)basis_to(q[j][v]), wr[v], acc[j]);
         }
     } else if (KIND == kReorth) {
 #pragma unroll
@@ -402,14 +486,14 @@ cgs2_pass_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __res
         T s1 = T(0);
 #pragma unroll
         for (int j = 0; j < KMAX; ++j)
-          if (j < ncol) s1 = fma(q[j][v], sh1[j], s1);
+          if (j < ncol) s1 = fma((T)basis_to(q[j][v]), sh1[j], s1);
         wr[v] = wr[v] - s1;   // w - Q h1
       }
 #pragma unroll
       for (int j = 0; j < KMAX; ++j)
         if (j < ncol) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[j] = fma(q[j][v], wr[v], acc[j]);
+          for (int v = 0; v < V; ++v) acc[j] = fma((T)basis_to(q[j][v]), wr[v], acc[j]);
         }
     } else {
 #pragma unroll
@@ -418,20 +502,24 @@ cgs2_pass_kernel(const T* __restrict__ Q, long long ns, int ncol, const T* __res
 #pragma unroll
         for (int j = 0; j < KMAX; ++j)
           if (j < ncol) {
-            s1 = fma(q[j][v], sh1[j], s1);
-            s2 = fma(q[j][v], sh2[j], s2);
+            const T qv = (T)basis_to(q[j][v]);
+            s1 = fma(qv, sh1[j], s1);
+            s2 = fma(qv, sh2[j], s2);
           }
         wr[v] = (wr[v] - s1) - s2;   // (w - Q h1) - Q h2
         acc[0] = fma(wr[v], wr[v], acc[0]);
+        if (MAXLAST) acc[1] = fmax(acc[1], fabs(wr[v]));
       }
-      st_group<T, V>(qnew + r0, wr);
+      st_group<T, V>(wout + r0, wr);
     }
   }
-  const int nred = KIND == kFinal ? 1 : ncol;
-  if (!block_partials_last<T, KMAX>(acc, nred, partials, counter, sums)) return;
+  const int nred = KIND == kFinal ? (MAXLAST ? 2 : 1) : ncol;
+  if (!block_partials_last<T, KMAX, MAXLAST>(acc, nred, partials, counter, sums)) return;
   if (KIND != kFinal) {
-    for (int j = threadIdx.x; j < nred; j += kRedThreads) out[j] = sums[j];
+    for (int j = threadIdx.x; j < nred; j += kRedThreads)
+      out[j] = S ? sums[j] * (double)qscale[j] : sums[j];
   } else if (threadIdx.x < 32) {
+    if (MAXLAST && threadIdx.x == 0) st->wmax = sums[1];
     arnoldi_givens_warp<KMAX>(sqrt(sums[0]), ncol - 1, h1, h2, H, ldh, cs, sn, t, st, next);
   }
 }
@@ -453,6 +541,37 @@ arnoldi_scale_kernel(T* __restrict__ qnew, long long ns, const SolveState* st) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) v[r] = v[r] * inv;
     Vec4<T>::st(qnew + (g << 2), v);
+  }
+}
+
+// Scaled basis: q_new = w'' / beta stored as u = w'' / max|w''| in B with
+// sigma = max|w''| / beta, and the dequantised sigma * u in FP32 (the next
+// V-cycle's input, so that it preconditions the vector the basis holds).
+template <typename B>
+__global__ void __launch_bounds__(256)
+arnoldi_quantize_kernel(const float* __restrict__ wpp, long long ns, B* __restrict__ qnew,
+                        float* __restrict__ qf, float* __restrict__ sigma_out,
+                        const SolveState* st) {
+  pdl_trigger();
+  pdl_wait();
+  const double beta = st->beta, m = st->wmax;
+  if (!(isfinite(beta) && beta > 0.0 && m > 0.0)) return;
+  const float inv_m = (float)(1.0 / m);
+  const float sigma = (float)(m / beta);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sigma_out = sigma;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (ns >> 3);
+       g += stride) {
+    float v[8];
+    ld_group<float, 8>(wpp + (g << 3), v);
+    B u[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      u[r] = basis_from<B>(v[r] * inv_m);
+      v[r] = sigma * basis_to(u[r]);
+    }
+    st_group<B, 8>(qnew + (g << 3), u);
+    st_group<float, 8>(qf + (g << 3), v);
   }
 }
 
@@ -479,27 +598,31 @@ __global__ void trsm_kernel(const double* __restrict__ H, int ldh, const double*
   }
 }
 
-// u = Q[:, :k] y (Algorithm 3, r <- Q t), k read from the solve state.
-template <typename T>
+// u = Q[:, :k] y (Algorithm 3, r <- Q t), k read from the solve state; a
+// scaled basis folds sigma_j into y_j.
+template <typename T, typename B>
 __global__ void __launch_bounds__(256)
-basis_combine_kernel(const T* __restrict__ Q, long long ns, const double* __restrict__ y,
-                     const SolveState* st, T* __restrict__ u) {
+basis_combine_kernel(const B* __restrict__ Q, long long ns, const double* __restrict__ y,
+                     const float* __restrict__ qscale, const SolveState* st,
+                     T* __restrict__ u) {
   pdl_trigger();
   pdl_wait();
   __shared__ T ys[kMaxRestart + 1];
   const int k = st->k;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = (T)y[j];
+  for (int j = threadIdx.x; j < k; j += blockDim.x)
+    ys[j] = (T)(basis_scaled<B>() ? y[j] * (double)qscale[j] : y[j]);
   __syncthreads();
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= (ns >> 2)) return;
   T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
   for (int j = 0; j < k; ++j) {
-    T q[4];
-    Vec4<T>::ld_cs(Q + j * ns + (g << 2), q);
+    B q[4];
+    ld_group<B, 4>(Q + j * ns + (g << 2), q);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) acc[r] = fma(q[r], ys[j], acc[r]);
+    for (int r = 0; r < 4; ++r) acc[r] = fma((T)basis_to(q[r]), ys[j], acc[r]);
   }
-  Vec4<T>::st(u + (g << 2), acc);
+  st_group<T, 4>(u + (g << 2), acc);
 }
 
 // x += d (Algorithm 3, mixed-precision update: FP64 accumulation).
@@ -512,7 +635,8 @@ update_x_kernel(double* __restrict__ x, const T* __restrict__ d, long long ns) {
   if (i < ns) x[i] += (double)d[i];
 }
 
-// r = b - A x and ||r||^2 (FP64).
+// r = b - A x, ||r||^2 and max |r| (FP64; the maximum scales q_0 of a
+// 2-byte basis).
 __global__ void __launch_bounds__(kRedThreads)
 residual_norm_kernel(const double* __restrict__ vals, const int* __restrict__ cols, long long ns,
                      const double* __restrict__ b, const double* __restrict__ x,
@@ -520,7 +644,7 @@ residual_norm_kernel(const double* __restrict__ vals, const int* __restrict__ co
                      unsigned int* counter, double* __restrict__ out) {
   pdl_trigger();
   pdl_wait();
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   const long long stride = (long long)gridDim.x * kRedThreads;
   for (long long row = blockIdx.x * (long long)kRedThreads + threadIdx.x; row < ns;
        row += stride) {
@@ -533,10 +657,11 @@ residual_norm_kernel(const double* __restrict__ vals, const int* __restrict__ co
     }
     r[row] = v;
     acc[0] = fma(v, v, acc[0]);
+    acc[1] = fmax(acc[1], fabs(v));
   }
-  __shared__ double sums[1];
-  if (block_partials_last<double, 1>(acc, 1, partials, counter, sums) && threadIdx.x == 0)
-    out[0] = sums[0];
+  __shared__ double sums[2];
+  if (block_partials_last<double, 2, true>(acc, 2, partials, counter, sums) && threadIdx.x < 2)
+    out[threadIdx.x] = sums[threadIdx.x];
 }
 
 // ||v||^2 of an FP64 vector.
@@ -584,18 +709,33 @@ __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* 
 }
 
 // Start of a restart cycle: q_0 = r / rho, t = rho e_1, k = 0; in graph mode
-// opens step 0's IF node and closes the others.
-template <typename T>
+// opens step 0's IF node and closes the others.  A scaled basis stores
+// u_0 = r / max|r| with sigma_0 = max|r| / rho and the dequantised q_0 in
+// FP32 for the first V-cycle.
+template <typename T, typename B>
 __global__ void __launch_bounds__(256)
-cycle_start_kernel(const double* __restrict__ r, long long ns, T* __restrict__ q0,
-                   double* __restrict__ t, SolveState* st,
+cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q0,
+                   float* __restrict__ qf, float* __restrict__ qscale,
+                   const double* __restrict__ rho2, double* __restrict__ t, SolveState* st,
                    const unsigned long long* __restrict__ handles, int nhandles) {
   pdl_trigger();
   pdl_wait();
   const double rho = st->rho;
-  const double inv = 1.0 / rho;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < ns) q0[i] = (T)(r[i] * inv);
+  if constexpr (basis_scaled<B>()) {
+    const double m = rho2[1];
+    const double inv = m > 0.0 ? 1.0 / m : 0.0;
+    const float sigma = (float)(m / rho);
+    if (i < ns) {
+      const B u = basis_from<B>((float)(r[i] * inv));
+      q0[i] = u;
+      qf[i] = sigma * basis_to(u);
+    }
+    if (i == 0) qscale[0] = sigma;
+  } else {
+    const double inv = 1.0 / rho;
+    if (i < ns) q0[i] = (T)(r[i] * inv);
+  }
   if (i == 0) {
     t[0] = rho;
     for (int j = 1; j <= st->m; ++j) t[j] = 0.0;
@@ -621,12 +761,12 @@ template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? HPG_FP64
 
 // Grid of a CGS2 pass: every resident block of the instantiation (one wave
 // of grid-stride blocks), at most the G blocks the partials are sized for.
-template <typename T, int KMAX, int KIND>
+template <typename T, typename B, int KMAX, int KIND>
 static int pass_grid(hpg_problem* h) {
   static int per_sm = 0;
   if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs2_pass_kernel<T, KMAX, KIND>,
-                                                      kRedThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, cgs2_pass_kernel<T, B, KMAX, KIND>, kRedThreads, 0) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
@@ -636,60 +776,83 @@ static int pass_grid(hpg_problem* h) {
   return g < h->ws->G ? g : h->ws->G;
 }
 
-template <typename T, int KMAX, int KIND>
-static cudaError_t enqueue_pass(hpg_problem* h, const T* Q, long long ns, int ncol, const T* w,
-                                T* qnew, double* out, int k, unsigned long long next,
+template <typename T, typename B, int KMAX, int KIND>
+static cudaError_t enqueue_pass(hpg_problem* h, const B* Q, long long ns, int ncol, const T* w,
+                                T* wout, double* out, int k, unsigned long long next,
                                 cudaStream_t s) {
   Workspace* ws = h->ws;
-  return kl(h, cgs2_pass_kernel<T, KMAX, KIND>, pass_grid<T, KMAX, KIND>(h), kRedThreads, s, Q,
-            ns, ncol, w, (const double*)ws->h1, (const double*)ws->h2, qnew, ws->partials,
-            ws->counter, out, ws->H, ws->m + 1, ws->cs, ws->sn, ws->t, ws->st, next);
+  return kl(h, cgs2_pass_kernel<T, B, KMAX, KIND>, pass_grid<T, B, KMAX, KIND>(h), kRedThreads,
+            s, Q, ns, ncol, w, (const float*)ws->qscale, (const double*)ws->h1,
+            (const double*)ws->h2, wout, ws->partials, ws->counter, out, ws->H, ws->m + 1,
+            ws->cs, ws->sn, ws->t, ws->st, next);
 }
 
 // One CGS2 pass over q_0..q_{ncol-1} (k = ncol - 1); the final pass also
 // forms the Arnoldi column and the Givens update and opens `next`.
-template <typename T, int KIND>
-static int launch_pass(hpg_problem* h, const T* Q, long long ns, int ncol, const T* w, T* qnew,
+template <typename T, typename B, int KIND>
+static int launch_pass(hpg_problem* h, const B* Q, long long ns, int ncol, const T* w, T* wout,
                        double* out, unsigned long long next, cudaStream_t s) {
   static const int cls[3] = {K_CGS2_GEMVT, K_CGS2_REORTH, K_CGS2_FINAL};
-  const double vecs = ncol + (KIND == kFinal ? 2 : 1);   // Q columns + w (+ q_new)
-  const double bytes = (double)h->lev[0].n * vecs * sizeof(T);
+  // Q columns + w (+ the w'' write)
+  const double bytes = (double)h->lev[0].n *
+                       (ncol * (double)sizeof(B) + (KIND == kFinal ? 2.0 : 1.0) * sizeof(T));
   const int k = ncol - 1;
   return launch(h, cls[KIND], 0, prec_of<T>(), bytes, s, "cgs2_pass_kernel", [&] {
-    if (ncol <= 8) return enqueue_pass<T, 8, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
-    if (ncol <= 16) return enqueue_pass<T, 16, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
-    if (ncol <= 32) return enqueue_pass<T, 32, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
-    return enqueue_pass<T, 64, KIND>(h, Q, ns, ncol, w, qnew, out, k, next, s);
+    if (ncol <= 8) return enqueue_pass<T, B, 8, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
+    if (ncol <= 16)
+      return enqueue_pass<T, B, 16, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
+    if (ncol <= 32)
+      return enqueue_pass<T, B, 32, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
+    return enqueue_pass<T, B, 64, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
   });
 }
 
 // One inner step k (0-based): z = M^{-1} q_k, w = A z, CGS2 against
 // q_0..q_k, q_{k+1} = w / ||w||, Givens update; `next` opens step k+1.
-template <typename T>
+// A scaled basis preconditions the dequantised q_k (qf) and quantises
+// q_{k+1} after the norm and max of w'' are known.
+template <typename T, typename B>
 static int enqueue_step(hpg_problem* h, int k, hpg_prec prec, unsigned long long next,
                         cudaStream_t s) {
   Workspace* ws = h->ws;
   const long long ns = h->lev[0].g.n_store;
-  T* Q = (T*)ws->Q;
+  B* Q = (B*)ws->Q;
   T* z = (T*)ws->z;
   T* w = (T*)ws->w;
+  constexpr bool S = basis_scaled<B>();
+  const void* r_in;
+  if constexpr (S) r_in = ws->qf;
+  else r_in = Q + (long long)k * ns;
   int rc;
-  if ((rc = run_vcycle(h, 0, prec, Q + (long long)k * ns, z, s))) return rc;
+  if ((rc = run_vcycle(h, 0, prec, r_in, z, s))) return rc;
   if ((rc = launch_spmv(h, 0, prec, z, w, s))) return rc;
   const int ncol = k + 1;
-  T* qnew = Q + (long long)(k + 1) * ns;
-  if ((rc = launch_pass<T, kGemvT>(h, Q, ns, ncol, w, nullptr, ws->h1, 0ULL, s))) return rc;
-  if ((rc = launch_pass<T, kReorth>(h, Q, ns, ncol, w, nullptr, ws->h2, 0ULL, s))) return rc;
-  if ((rc = launch_pass<T, kFinal>(h, Q, ns, ncol, w, qnew, nullptr, next, s))) return rc;
-  return launch(h, K_ARNOLDI_SCALE, 0, prec_of<T>(), 2.0 * h->lev[0].n * sizeof(T), s,
-                "arnoldi_scale_kernel", [&] {
-                  return kl(h, arnoldi_scale_kernel<T>, grid_for(ns / 4, 256), 256, s, qnew, ns,
-                            (const SolveState*)ws->st);
-                });
+  B* qnew = Q + (long long)(k + 1) * ns;
+  T* wout;
+  if constexpr (S) wout = w;   // w'' in place, quantised below
+  else wout = qnew;
+  if ((rc = launch_pass<T, B, kGemvT>(h, Q, ns, ncol, w, nullptr, ws->h1, 0ULL, s))) return rc;
+  if ((rc = launch_pass<T, B, kReorth>(h, Q, ns, ncol, w, nullptr, ws->h2, 0ULL, s))) return rc;
+  if ((rc = launch_pass<T, B, kFinal>(h, Q, ns, ncol, w, wout, nullptr, next, s))) return rc;
+  if constexpr (S) {
+    return launch(h, K_ARNOLDI_SCALE, 0, prec_of<T>(),
+                  h->lev[0].n * (2.0 * sizeof(T) + sizeof(B)), s, "arnoldi_quantize_kernel",
+                  [&] {
+                    return kl(h, arnoldi_quantize_kernel<B>, grid_for(ns / 8, 256), 256, s,
+                              (const float*)w, ns, qnew, ws->qf, ws->qscale + k + 1,
+                              (const SolveState*)ws->st);
+                  });
+  } else {
+    return launch(h, K_ARNOLDI_SCALE, 0, prec_of<T>(), 2.0 * h->lev[0].n * sizeof(T), s,
+                  "arnoldi_scale_kernel", [&] {
+                    return kl(h, arnoldi_scale_kernel<T>, grid_for(ns / 4, 256), 256, s, qnew,
+                              ns, (const SolveState*)ws->st);
+                  });
+  }
 }
 
 // End of a cycle: y = H^{-1} t, u = Q y, d = M^{-1} u, x += d.
-template <typename T>
+template <typename T, typename B>
 static int enqueue_cycle_update(hpg_problem* h, hpg_prec prec, int k_model, cudaStream_t s) {
   Workspace* ws = h->ws;
   const long long ns = h->lev[0].g.n_store;
@@ -700,11 +863,11 @@ static int enqueue_cycle_update(hpg_problem* h, hpg_prec prec, int k_model, cuda
               ws->y, (const SolveState*)ws->st);
   });
   if (rc) return rc;
-  rc = launch(h, K_COMBINE, 0, prec_of<T>(), n * (k_model + 1) * sizeof(T), s,
+  rc = launch(h, K_COMBINE, 0, prec_of<T>(), n * (k_model * (double)sizeof(B) + sizeof(T)), s,
               "basis_combine_kernel", [&] {
-                return kl(h, basis_combine_kernel<T>, grid_for(ns / 4, 256), 256, s,
-                          (const T*)ws->Q, ns, (const double*)ws->y, (const SolveState*)ws->st,
-                          (T*)ws->u);
+                return kl(h, basis_combine_kernel<T, B>, grid_for(ns / 4, 256), 256, s,
+                          (const B*)ws->Q, ns, (const double*)ws->y,
+                          (const float*)ws->qscale, (const SolveState*)ws->st, (T*)ws->u);
               });
   if (rc) return rc;
   if ((rc = run_vcycle(h, 0, prec, ws->u, ws->z, s))) return rc;
@@ -732,15 +895,17 @@ static int enqueue_outer(hpg_problem* h, unsigned long long loop, cudaStream_t s
   });
 }
 
-template <typename T>
+template <typename T, typename B>
 static int enqueue_cycle_start(hpg_problem* h, const unsigned long long* handles, int nh,
                                cudaStream_t s) {
   Workspace* ws = h->ws;
   const long long ns = h->lev[0].g.n_store;
-  return launch(h, K_CYCLE_START, 0, prec_of<T>(), h->lev[0].n * (8.0 + sizeof(T)), s,
+  const double row_bytes = 8.0 + sizeof(B) + (basis_scaled<B>() ? sizeof(float) : 0.0);
+  return launch(h, K_CYCLE_START, 0, prec_of<T>(), h->lev[0].n * row_bytes, s,
                 "cycle_start_kernel", [&] {
-                  return kl(h, cycle_start_kernel<T>, grid_for(ns, 256), 256, s,
-                            (const double*)ws->r, ns, (T*)ws->Q, ws->t, ws->st, handles, nh);
+                  return kl(h, cycle_start_kernel<T, B>, grid_for(ns, 256), 256, s,
+                            (const double*)ws->r, ns, (B*)ws->Q, ws->qf, ws->qscale,
+                            (const double*)ws->rho2, ws->t, ws->st, handles, nh);
                 });
 }
 
@@ -788,10 +953,11 @@ static int append_conditional(hpg_problem* h, cudaStream_t s, cudaGraphCondition
 //     -> TRSM, Q y, V-cycle, x += d -> outer residual + test }
 // Each step's Givens kernel opens the next step's IF node while the cycle
 // continues, so converged cycles skip the remaining steps on the device.
-template <typename T>
+template <typename T, typename B>
 static int capture_solve_graph(hpg_problem* h, int m, hpg_prec prec) {
   Workspace* ws = h->ws;
-  if (ws->exec && ws->graph_m == m && ws->graph_prec == prec) return HPG_OK;
+  if (ws->exec && ws->graph_m == m && ws->graph_prec == prec && ws->graph_basis == ws->basis)
+    return HPG_OK;
   if (ws->exec) cudaGraphExecDestroy(ws->exec);
   if (ws->graph) cudaGraphDestroy(ws->graph);
   ws->exec = nullptr;
@@ -825,7 +991,7 @@ static int capture_solve_graph(hpg_problem* h, int m, hpg_prec prec) {
   HPG_CK(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, mode));
   h->pdl_next = false;
   mark = h->launches;
-  rc = enqueue_cycle_start<T>(h, ws->hk, m, s1);
+  rc = enqueue_cycle_start<T, B>(h, ws->hk, m, s1);
   ws->n_start = h->launches - mark;
   for (int k = 0; k < m && rc == HPG_OK; ++k) {
     cudaGraph_t sb = nullptr;
@@ -838,7 +1004,7 @@ static int capture_solve_graph(hpg_problem* h, int m, hpg_prec prec) {
     }
     h->pdl_next = false;
     mark = h->launches;
-    rc = enqueue_step<T>(h, k, prec, k + 1 < m ? (unsigned long long)hk[k + 1] : 0ULL, s2);
+    rc = enqueue_step<T, B>(h, k, prec, k + 1 < m ? (unsigned long long)hk[k + 1] : 0ULL, s2);
     ws->n_step = h->launches - mark;
     cudaGraph_t sb_end = nullptr;
     e = cudaStreamEndCapture(s2, &sb_end);
@@ -846,7 +1012,7 @@ static int capture_solve_graph(hpg_problem* h, int m, hpg_prec prec) {
       rc = cuda_fail(e, "cudaStreamEndCapture(step)", __FILE__, __LINE__);
   }
   mark = h->launches;
-  if (rc == HPG_OK) rc = enqueue_cycle_update<T>(h, prec, m / 2, s1);
+  if (rc == HPG_OK) rc = enqueue_cycle_update<T, B>(h, prec, m / 2, s1);
   ws->n_update = h->launches - mark;
   if (rc == HPG_OK) rc = enqueue_outer(h, (unsigned long long)loop, s1);
   h->launches = launches_before;   // capture enqueues nothing that runs
@@ -866,6 +1032,7 @@ static int capture_solve_graph(hpg_problem* h, int m, hpg_prec prec) {
   ws->graph_nodes = (int)nn;
   ws->graph_m = m;
   ws->graph_prec = prec;
+  ws->graph_basis = ws->basis;
   h->pdl_next = false;
   return HPG_OK;
 }
@@ -879,11 +1046,11 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-template <typename T>
+template <typename T, typename B>
 static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m, int maxit,
-                   hpg_prec prec, hpg_solve_info* info, cudaStream_t s) {
+                   hpg_prec prec, hpg_prec basis, hpg_solve_info* info, cudaStream_t s) {
   int rc;
-  if ((rc = ensure_workspace(h, m, prec))) return rc;
+  if ((rc = ensure_workspace(h, m, prec, basis))) return rc;
   Workspace* ws = h->ws;
   const Level& L = h->lev[0];
   const long long ns = L.g.n_store, n = L.n;
@@ -938,7 +1105,7 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
     HPG_CK(cudaMemcpyAsync(ws->st, ws->st_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
     h->pdl_next = false;
     if (use_graph) {
-      if ((rc = capture_solve_graph<T>(h, m, prec))) return rc;
+      if ((rc = capture_solve_graph<T, B>(h, m, prec))) return rc;
       HPG_CK(cudaGraphLaunch(ws->exec, s));
       graph_launches = 1;
       h->pdl_next = false;
@@ -948,18 +1115,18 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
       if ((rc = enqueue_outer(h, 0ULL, s))) return rc;
       if ((rc = read_state(h, s))) return rc;
       while (!ws->st_host->done) {
-        if ((rc = enqueue_cycle_start<T>(h, nullptr, 0, s))) return rc;
+        if ((rc = enqueue_cycle_start<T, B>(h, nullptr, 0, s))) return rc;
         for (int k = 0; k < m; ++k) {
           if (h->profiling) {
             // instrumentation only: not counted with the solve's kernels
             HPG_CK(kl(h, delay_kernel, 1, 32, s, 4000000LL));
             h->pdl_next = false;
           }
-          if ((rc = enqueue_step<T>(h, k, prec, 0ULL, s))) return rc;
+          if ((rc = enqueue_step<T, B>(h, k, prec, 0ULL, s))) return rc;
           if ((rc = read_state(h, s))) return rc;
           if (!ws->st_host->active) break;
         }
-        if ((rc = enqueue_cycle_update<T>(h, prec, ws->st_host->k, s))) return rc;
+        if ((rc = enqueue_cycle_update<T, B>(h, prec, ws->st_host->k, s))) return rc;
         if ((rc = enqueue_outer(h, 0ULL, s))) return rc;
         if ((rc = read_state(h, s))) return rc;
       }
@@ -1035,15 +1202,24 @@ HPG_API int hpg_gmres_ir_solve(hpg_problem_t* h, const double* b, double* x, dou
     if (info) info->status = HPG_ERR_STATE;
     return HPG_ERR_STATE;
   }
-  if ((inner != HPG_FP64 && inner != HPG_FP32) || basis != inner) {
-    set_error("hpg_gmres_ir_solve: inner %d / basis %d not supported (basis must equal inner)",
+  const bool ok = (inner == HPG_FP64 && basis == HPG_FP64) ||
+                  (inner == HPG_FP32 &&
+                   (basis == HPG_FP32 || basis == HPG_BF16 || basis == HPG_FP16));
+  if (!ok) {
+    set_error("hpg_gmres_ir_solve: inner %d / basis %d not supported (FP64/FP64, or FP32 inner "
+              "with an FP32, BF16 or FP16 basis)",
               (int)inner, (int)basis);
     if (info) info->status = HPG_ERR_UNSUPPORTED;
     return HPG_ERR_UNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (inner == HPG_FP64) return solve_t<double>(h, b, x, tol, restart, maxit, inner, info, s);
-  return solve_t<float>(h, b, x, tol, restart, maxit, inner, info, s);
+  if (inner == HPG_FP64)
+    return solve_t<double, double>(h, b, x, tol, restart, maxit, inner, basis, info, s);
+  if (basis == HPG_BF16)
+    return solve_t<float, __nv_bfloat16>(h, b, x, tol, restart, maxit, inner, basis, info, s);
+  if (basis == HPG_FP16)
+    return solve_t<float, __half>(h, b, x, tol, restart, maxit, inner, basis, info, s);
+  return solve_t<float, float>(h, b, x, tol, restart, maxit, inner, basis, info, s);
 }
 
 }  // extern "C"

@@ -26,6 +26,7 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--maxit", type=int, default=10000)
     ap.add_argument("--inner", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--basis", choices=["same", "bf16", "fp16"], default="same")
     ap.add_argument("--noise", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--solves", type=int, default=1)
@@ -39,6 +40,7 @@ def main(argv=None):
     build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     inner = hpg.HPG_FP32 if a.inner == "fp32" else hpg.HPG_FP64
+    basis = {"same": inner, "bf16": hpg.HPG_BF16, "fp16": hpg.HPG_FP16}[a.basis]
     with hpg.Problem(*a.grid, beta=a.beta, levels=a.levels) as p:
         n = a.grid[0] * a.grid[1] * a.grid[2]
         ones = torch.ones(n, dtype=torch.float64, device=dev)
@@ -51,7 +53,7 @@ def main(argv=None):
         for _ in range(a.warmup):
             x.zero_()
             hpg.gmres_ir_solve(p.h, b, x, tol=a.tol, restart=a.restart, maxit=a.maxit,
-                               inner=inner)
+                               inner=inner, basis=basis)
         if a.profile:
             hpg.set_profiling(p.h, True)
         for _ in range(a.solves):
@@ -59,7 +61,7 @@ def main(argv=None):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             info = hpg.gmres_ir_solve(p.h, b, x, tol=a.tol, restart=a.restart, maxit=a.maxit,
-                                      inner=inner)
+                                      inner=inner, basis=basis)
             info["ms"] = 1e3 * (time.perf_counter() - t0)
             print(json.dumps(info), flush=True)
         if a.profile:

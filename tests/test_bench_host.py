@@ -92,5 +92,6 @@ def test_gs_traffic_only_for_unchanged_kernel_sources(monkeypatch):
     assert bench.gs_traffic() is None
     monkeypatch.setitem(bench.GS_TRAFFIC, "sources_sha256", bench.gs_sources_sha256())
     assert bench.gs_traffic() == 1.0e6
+    assert bench.gs_traffic("mxp_gmres50_320cube") is None
     monkeypatch.setitem(bench.GS_TRAFFIC, "bytes_per_launch", None)
     assert bench.gs_traffic() is None
