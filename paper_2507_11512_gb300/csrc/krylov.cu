@@ -206,11 +206,9 @@ template <> struct Vec4<double> {
 // ----------------------------------------------------------------- CGS2
 // Pass kinds of the three-pass CGS2 (Algorithm 3, CGS2 procedure):
 //   kGemvT:   h1 = Q^T w                                     (GEMVT)
-//   kReorth:  h2 = Q^T (w - Q h1)                            (GEMV + reorth GEMVT)
-//   kFinal:   q_new = (w - Q h1) - Q h2, ||q_new||^2,        (reorth GEMV + norm)
+//   kReorth:  w' = w - Q h1 (stored), h2 = Q^T w'            (GEMV + reorth GEMVT)
+//   kFinal:   q_new = w' - Q h2, ||q_new||^2                 (reorth GEMV + norm)
 //             then (last block) the Arnoldi column and the Givens update
-// The GEMV w - Q h1 is recomputed row-locally in the last pass (same code,
-// same rounding) instead of being stored.
 //
 // Each pass streams w and the k+1 basis columns once.  A thread takes a row
 // group of V consecutive rows per grid-stride iteration and issues one
@@ -260,50 +258,98 @@ __host__ __device__ constexpr int pass_min_blocks() {
 
 // V consecutive elements (V * sizeof(E) bytes, aligned to that size up to 16:
 // storage rows come in multiples of 32), streaming loads / plain stores.
+// FP32 and FP64 elements move as float/double vector types (moving them
+// through integer vectors measured up to 2x slower for FP64 passes); 2-byte
+// elements move as packed integers.
 template <typename E, int V>
 __device__ __forceinline__ void ld_group(const E* p, E (&v)[V]) {
-  constexpr int bytes = (int)sizeof(E) * V;
-  if constexpr (bytes % 16 == 0) {
+  if constexpr (sizeof(E) == 8 && V == 1) {
+    v[0] = __ldcs(p);
+  } else if constexpr (sizeof(E) == 8) {
+    static_assert(V % 2 == 0, "FP64 row groups of 1 or 2k elements");
 #pragma unroll
-    for (int i = 0; i < bytes / 16; ++i) {
-      const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p) + i);
-      memcpy(reinterpret_cast<char*>(v) + 16 * i, &t, 16);
+    for (int i = 0; i < V / 2; ++i) {
+      const double2 t = __ldcs(reinterpret_cast<const double2*>(p) + i);
+      v[2 * i] = t.x;
+      v[2 * i + 1] = t.y;
     }
-  } else if constexpr (bytes == 8) {
-    const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
-    memcpy(v, &t, 8);
-  } else if constexpr (bytes == 4) {
-    const unsigned t = __ldcs(reinterpret_cast<const unsigned*>(p));
-    memcpy(v, &t, 4);
+  } else if constexpr (sizeof(E) == 4 && V % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i) {
+      const float4 t = __ldcs(reinterpret_cast<const float4*>(p) + i);
+      v[4 * i] = t.x;
+      v[4 * i + 1] = t.y;
+      v[4 * i + 2] = t.z;
+      v[4 * i + 3] = t.w;
+    }
+  } else if constexpr (sizeof(E) == 4 && V == 2) {
+    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else if constexpr (sizeof(E) == 4) {
+    static_assert(V == 1, "FP32 row groups of 1, 2 or 4k elements");
+    v[0] = __ldcs(p);
   } else {
-    static_assert(bytes == 2, "row group of 2 to 16k bytes");
-    const unsigned short t = __ldcs(reinterpret_cast<const unsigned short*>(p));
-    memcpy(v, &t, 2);
+    static_assert(sizeof(E) == 2, "2-, 4- or 8-byte elements");
+    constexpr int bytes = 2 * V;
+    if constexpr (bytes % 16 == 0) {
+#pragma unroll
+      for (int i = 0; i < bytes / 16; ++i) {
+        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p) + i);
+        memcpy(reinterpret_cast<char*>(v) + 16 * i, &t, 16);
+      }
+    } else if constexpr (bytes == 8) {
+      const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
+      memcpy(v, &t, 8);
+    } else if constexpr (bytes == 4) {
+      const unsigned t = __ldcs(reinterpret_cast<const unsigned*>(p));
+      memcpy(v, &t, 4);
+    } else {
+      static_assert(bytes == 2, "2-byte row groups of 1, 2, 4 or 8k elements");
+      const unsigned short t = __ldcs(reinterpret_cast<const unsigned short*>(p));
+      memcpy(v, &t, 2);
+    }
   }
 }
 template <typename E, int V>
 __device__ __forceinline__ void st_group(E* p, const E (&v)[V]) {
-  constexpr int bytes = (int)sizeof(E) * V;
-  if constexpr (bytes % 16 == 0) {
+  if constexpr (sizeof(E) == 8 && V == 1) {
+    *p = v[0];
+  } else if constexpr (sizeof(E) == 8) {
 #pragma unroll
-    for (int i = 0; i < bytes / 16; ++i) {
-      uint4 t;
-      memcpy(&t, reinterpret_cast<const char*>(v) + 16 * i, 16);
-      reinterpret_cast<uint4*>(p)[i] = t;
-    }
-  } else if constexpr (bytes == 8) {
-    uint2 t;
-    memcpy(&t, v, 8);
-    *reinterpret_cast<uint2*>(p) = t;
-  } else if constexpr (bytes == 4) {
-    unsigned t;
-    memcpy(&t, v, 4);
-    *reinterpret_cast<unsigned*>(p) = t;
+    for (int i = 0; i < V / 2; ++i)
+      reinterpret_cast<double2*>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  } else if constexpr (sizeof(E) == 4 && V % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i)
+      reinterpret_cast<float4*>(p)[i] =
+          make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else if constexpr (sizeof(E) == 4 && V == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (sizeof(E) == 4) {
+    *p = v[0];
   } else {
-    static_assert(bytes == 2, "row group of 2 to 16k bytes");
-    unsigned short t;
-    memcpy(&t, v, 2);
-    *reinterpret_cast<unsigned short*>(p) = t;
+    constexpr int bytes = 2 * V;
+    if constexpr (bytes % 16 == 0) {
+#pragma unroll
+      for (int i = 0; i < bytes / 16; ++i) {
+        uint4 t;
+        memcpy(&t, reinterpret_cast<const char*>(v) + 16 * i, 16);
+        reinterpret_cast<uint4*>(p)[i] = t;
+      }
+    } else if constexpr (bytes == 8) {
+      uint2 t;
+      memcpy(&t, v, 8);
+      *reinterpret_cast<uint2*>(p) = t;
+    } else if constexpr (bytes == 4) {
+      unsigned t;
+      memcpy(&t, v, 4);
+      *reinterpret_cast<unsigned*>(p) = t;
+    } else {
+      unsigned short t;
+      memcpy(&t, v, 2);
+      *reinterpret_cast<unsigned short*>(p) = t;
+    }
   }
 }
 
@@ -433,10 +479,16 @@ __device__ void arnoldi_givens_warp(double beta, int k, const double* __restrict
 
 // One CGS2 pass (kind KIND) over the basis columns q_0..q_{ncol-1} stored as
 // B (scaled by qscale[j] when B is a 2-byte format: the scales are folded into
-// the coefficients and the results, so the inner loop only converts).  The
-// final pass writes w'' = (w - Q h1) - Q h2 to `wout` in T (a basis column
-// when B == T; w itself, in place, for a scaled basis, whose quantisation
-// needs max |w''| first) and reduces ||w''||^2 (and max |w''|).
+// the coefficients and the results, so the inner loop only converts).
+//   kGemvT:  h1 = Q^T w
+//   kReorth: w' = w - Q h1, written over w in place (wout == w), h2 = Q^T w'
+//   kFinal:  w'' = w' - Q h2 written to `wout` in T (a basis column when
+//            B == T; w itself, in place, for a scaled basis, whose
+//            quantisation needs max |w''| first), ||w''||^2 (and max |w''|),
+//            then (last block) the Arnoldi column and the Givens update.
+// Storing w' costs one vector write and saves the final pass a second GEMV
+// (FP64 passes are close to the FP64 FMA rate of this GPU); the values are
+// those of recomputing it (same operands, same order).
 template <typename T, typename B, int KMAX, int KIND>
 __global__ void __launch_bounds__(kRedThreads, (pass_min_blocks<T, KMAX>()))
 cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
@@ -448,16 +500,14 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
   constexpr int V = pass_vec<B, KMAX>();
   constexpr bool S = basis_scaled<B>();
   constexpr bool MAXLAST = S && KIND == kFinal;
-  __shared__ T sh1[KMAX], sh2[KMAX];
+  __shared__ T shc[KMAX];   // h1 (reorth) or h2 (final), scaled for a 2-byte basis
   __shared__ double sums[KMAX];
   pdl_trigger();
   pdl_wait();   // w, Q and h come from earlier kernels
   if (KIND != kGemvT) {
-    for (int j = threadIdx.x; j < ncol; j += kRedThreads) {
-      const double sj = S ? (double)qscale[j] : 1.0;
-      sh1[j] = (T)(S ? h1[j] * sj : h1[j]);
-      if (KIND == kFinal) sh2[j] = (T)(S ? h2[j] * sj : h2[j]);
-    }
+    const double* hc = KIND == kReorth ? h1 : h2;
+    for (int j = threadIdx.x; j < ncol; j += kRedThreads)
+      shc[j] = (T)(S ? hc[j] * (double)qscale[j] : hc[j]);
     __syncthreads();
   }
   T acc[KMAX];
@@ -465,14 +515,17 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
   for (int j = 0; j < KMAX; ++j) acc[j] = T(0);
   const long long ng = ns / V;
   const long long stride = (long long)gridDim.x * kRedThreads;
-  for (long long g = blockIdx.x * (long long)kRedThreads + threadIdx.x; g < ng; g += stride) {
-    const long long r0 = g * V;
-    T wr[V];
-    ld_group<T, V>(w + r0, wr);
-    B q[KMAX][V];
+  auto load = [&](long long g, T (&wr)[V], B (&q)[KMAX][V]) {
+    ld_group<T, V>(w + g * V, wr);
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-      if (j < ncol) ld_group<B, V>(Q + j * ns + r0, q[j]);
+      if (j < ncol) ld_group<B, V>(Q + j * ns + g * V, q[j]);
+  };
+  for (long long g = blockIdx.x * (long long)kRedThreads + threadIdx.x; g < ng; g += stride) {
+    T wr[V];
+    B q[KMAX][V];
+    load(g, wr, q);
+    const long long r0 = g * V;
     if (KIND == kGemvT) {
 #pragma unroll
       for (int j = 0; j < KMAX; ++j)
@@ -480,37 +533,46 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
 #pragma unroll
           for (int v = 0; v < V; ++v) acc[j] = fma((T)basis_to(q[j][v]), wr[v], acc[j]);
         }
-    } else if (KIND == kReorth) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        T s1 = T(0);
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j)
-          if (j < ncol) s1 = fma((T)basis_to(q[j][v]), sh1[j], s1);
-        wr[v] = wr[v] - s1;   // w - Q h1
-      }
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < ncol) {
-#pragma unroll
-          for (int v = 0; v < V; ++v) acc[j] = fma((T)basis_to(q[j][v]), wr[v], acc[j]);
-        }
     } else {
+      // s = (Q c)_row, c = h1 or h2.  Rows always sum over j in ascending
+      // order; for a 2-byte basis (8 rows per thread) the column-outer order
+      // reads each coefficient from shared memory once per row group
+      // (measured faster there, slower for FP32/FP64 rows).
+      T sc[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        T s1 = T(0), s2 = T(0);
+      for (int v = 0; v < V; ++v) sc[v] = T(0);
+      if constexpr (S) {
 #pragma unroll
         for (int j = 0; j < KMAX; ++j)
           if (j < ncol) {
-            const T qv = (T)basis_to(q[j][v]);
-            s1 = fma(qv, sh1[j], s1);
-            s2 = fma(qv, sh2[j], s2);
+            const T c = shc[j];
+#pragma unroll
+            for (int v = 0; v < V; ++v) sc[v] = fma((T)basis_to(q[j][v]), c, sc[v]);
           }
-        wr[v] = (wr[v] - s1) - s2;   // (w - Q h1) - Q h2
-        acc[0] = fma(wr[v], wr[v], acc[0]);
-        if (MAXLAST) acc[1] = fmax(acc[1], fabs(wr[v]));
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int j = 0; j < KMAX; ++j)
+            if (j < ncol) sc[v] = fma((T)basis_to(q[j][v]), shc[j], sc[v]);
       }
+#pragma unroll
+      for (int v = 0; v < V; ++v) wr[v] = wr[v] - sc[v];   // w' = w - Q h1 / w'' = w' - Q h2
       st_group<T, V>(wout + r0, wr);
+      if (KIND == kReorth) {
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+          if (j < ncol) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[j] = fma((T)basis_to(q[j][v]), wr[v], acc[j]);
+          }
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          acc[0] = fma(wr[v], wr[v], acc[0]);
+          if (MAXLAST) acc[1] = fmax(acc[1], fabs(wr[v]));
+        }
+      }
     }
   }
   const int nred = KIND == kFinal ? (MAXLAST ? 2 : 1) : ncol;
@@ -530,9 +592,17 @@ __global__ void __launch_bounds__(256)
 arnoldi_scale_kernel(T* __restrict__ qnew, long long ns, const SolveState* st) {
   pdl_trigger();
   pdl_wait();
-  const double beta = st->beta;
-  if (!(isfinite(beta) && beta > 0.0)) return;
-  const T inv = (T)(1.0 / beta);
+  // one FP64 division per block (FP64 throughput is low on this GPU)
+  __shared__ T s_inv;
+  __shared__ bool s_ok;
+  if (threadIdx.x == 0) {
+    const double beta = st->beta;
+    s_ok = isfinite(beta) && beta > 0.0;
+    s_inv = s_ok ? (T)(1.0 / beta) : T(0);
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const T inv = s_inv;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (ns >> 2);
        g += stride) {
@@ -554,24 +624,31 @@ arnoldi_quantize_kernel(const float* __restrict__ wpp, long long ns, B* __restri
                         const SolveState* st) {
   pdl_trigger();
   pdl_wait();
-  const double beta = st->beta, m = st->wmax;
-  if (!(isfinite(beta) && beta > 0.0 && m > 0.0)) return;
-  const float inv_m = (float)(1.0 / m);
-  const float sigma = (float)(m / beta);
+  __shared__ float s_inv_m, s_sigma;
+  __shared__ bool s_ok;
+  if (threadIdx.x == 0) {
+    const double beta = st->beta, m = st->wmax;
+    s_ok = isfinite(beta) && beta > 0.0 && m > 0.0;
+    s_inv_m = s_ok ? (float)(1.0 / m) : 0.0f;
+    s_sigma = s_ok ? (float)(m / beta) : 0.0f;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const float inv_m = s_inv_m, sigma = s_sigma;
   if (blockIdx.x == 0 && threadIdx.x == 0) *sigma_out = sigma;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (ns >> 3);
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (ns >> 2);
        g += stride) {
-    float v[8];
-    ld_group<float, 8>(wpp + (g << 3), v);
-    B u[8];
+    float v[4];
+    ld_group<float, 4>(wpp + (g << 2), v);
+    B u[4];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < 4; ++r) {
       u[r] = basis_from<B>(v[r] * inv_m);
       v[r] = sigma * basis_to(u[r]);
     }
-    st_group<B, 8>(qnew + (g << 3), u);
-    st_group<float, 8>(qf + (g << 3), v);
+    st_group<B, 4>(qnew + (g << 2), u);
+    st_group<float, 4>(qf + (g << 2), v);
   }
 }
 
@@ -720,12 +797,24 @@ cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q
                    const unsigned long long* __restrict__ handles, int nhandles) {
   pdl_trigger();
   pdl_wait();
+  // the scalars once per block (one FP64 division each)
+  __shared__ double s_inv;
+  __shared__ float s_sigma;
   const double rho = st->rho;
+  if (threadIdx.x == 0) {
+    if constexpr (basis_scaled<B>()) {
+      const double m = rho2[1];
+      s_inv = m > 0.0 ? 1.0 / m : 0.0;
+      s_sigma = (float)(m / rho);
+    } else {
+      s_inv = 1.0 / rho;
+    }
+  }
+  __syncthreads();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if constexpr (basis_scaled<B>()) {
-    const double m = rho2[1];
-    const double inv = m > 0.0 ? 1.0 / m : 0.0;
-    const float sigma = (float)(m / rho);
+    const double inv = s_inv;
+    const float sigma = s_sigma;
     if (i < ns) {
       const B u = basis_from<B>((float)(r[i] * inv));
       q0[i] = u;
@@ -733,7 +822,7 @@ cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q
     }
     if (i == 0) qscale[0] = sigma;
   } else {
-    const double inv = 1.0 / rho;
+    const double inv = s_inv;
     if (i < ns) q0[i] = (T)(r[i] * inv);
   }
   if (i == 0) {
@@ -793,9 +882,9 @@ template <typename T, typename B, int KIND>
 static int launch_pass(hpg_problem* h, const B* Q, long long ns, int ncol, const T* w, T* wout,
                        double* out, unsigned long long next, cudaStream_t s) {
   static const int cls[3] = {K_CGS2_GEMVT, K_CGS2_REORTH, K_CGS2_FINAL};
-  // Q columns + w (+ the w'' write)
+  // Q columns + w (+ the w' / w'' write)
   const double bytes = (double)h->lev[0].n *
-                       (ncol * (double)sizeof(B) + (KIND == kFinal ? 2.0 : 1.0) * sizeof(T));
+                       (ncol * (double)sizeof(B) + (KIND == kGemvT ? 1.0 : 2.0) * sizeof(T));
   const int k = ncol - 1;
   return launch(h, cls[KIND], 0, prec_of<T>(), bytes, s, "cgs2_pass_kernel", [&] {
     if (ncol <= 8) return enqueue_pass<T, B, 8, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
@@ -832,13 +921,13 @@ static int enqueue_step(hpg_problem* h, int k, hpg_prec prec, unsigned long long
   if constexpr (S) wout = w;   // w'' in place, quantised below
   else wout = qnew;
   if ((rc = launch_pass<T, B, kGemvT>(h, Q, ns, ncol, w, nullptr, ws->h1, 0ULL, s))) return rc;
-  if ((rc = launch_pass<T, B, kReorth>(h, Q, ns, ncol, w, nullptr, ws->h2, 0ULL, s))) return rc;
+  if ((rc = launch_pass<T, B, kReorth>(h, Q, ns, ncol, w, w, ws->h2, 0ULL, s))) return rc;
   if ((rc = launch_pass<T, B, kFinal>(h, Q, ns, ncol, w, wout, nullptr, next, s))) return rc;
   if constexpr (S) {
     return launch(h, K_ARNOLDI_SCALE, 0, prec_of<T>(),
                   h->lev[0].n * (2.0 * sizeof(T) + sizeof(B)), s, "arnoldi_quantize_kernel",
                   [&] {
-                    return kl(h, arnoldi_quantize_kernel<B>, grid_for(ns / 8, 256), 256, s,
+                    return kl(h, arnoldi_quantize_kernel<B>, grid_for(ns / 4, 256), 256, s,
                               (const float*)w, ns, qnew, ws->qf, ws->qscale + k + 1,
                               (const SolveState*)ws->st);
                   });
