@@ -47,6 +47,11 @@ in the design notes of the repository):
   j = 1..k-1 to column k, then form the rotation that zeroes H[k+1, k].
 * inner test: the Givens estimate rho = |t_{k+1}| against tau * ||b||.
 * iteration count: the total number of inner (Arnoldi) steps.
+
+The differentiable solve (``dense_adjoint_gradients``) has no counterpart in
+the paper: it is the plain definition of the gradient of a loss through
+A(theta) x = b by the adjoint equation, written with dense LAPACK solves for
+tiny grids.
 """
 
 import math
@@ -386,3 +391,26 @@ def stencil_row(nx, ny, nz, i, j, k, beta=0.0, theta_ijk=1.0):
                 v = off_diagonal_value(dx, dy, dz, beta)
             row.append((natural_index(ni, nj, nk, nx, ny), v))
     return row
+
+
+# ----------------------------------------------------- differentiable solve --
+def dense_adjoint_gradients(nx, ny, nz, b, x_target, beta=0.0, theta=None):
+    """x = A(theta)^{-1} b, L = ||x - x_target||^2 and its gradients by the
+    adjoint equation, with dense LU solves (tiny grids only).
+
+    dL/dx = 2 (x - x_target); the adjoint lambda solves A^T lambda = dL/dx;
+    dL/db = lambda; and since only a_ii = 26 theta_i depends on theta_i,
+    dL/dtheta_i = -lambda_i * 26 * x_i.  A^T is formed by transposing A here
+    (not by flipping beta), so the transpose reading is checked, not assumed.
+    Returns (x, L, dL/db, dL/dtheta).
+    """
+    n = nx * ny * nz
+    if theta is None:
+        theta = np.ones(n)
+    A = build_matrix(nx, ny, nz, beta, theta).toarray()
+    x = np.linalg.solve(A, b)
+    r = x - x_target
+    L = float(r @ r)
+    lam = np.linalg.solve(A.T, 2.0 * r)
+    return x, L, lam, -26.0 * lam * x
+
