@@ -68,6 +68,10 @@ def parse():
                     help="storage of the Krylov basis in the mixed-precision solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--validation", default="standard", choices=["standard", "fullscale"],
+                    help="validation phase for the penalty n_d/n_ir (Sec. 3, Sec. 3.3)")
+    ap.add_argument("--nd-max", type=int, default=10000,
+                    help="FP64 iteration cap of the validation phase")
     ap.add_argument("--cpu-sample-iters", type=int, default=8)
     return ap.parse_args()
 
@@ -295,6 +299,19 @@ def run_gpu(args):
                 "ms_per_solve": ms64_max / len(infos64), "iterations": n_d,
                 "rel_residual": infos64[-1]["rel_residual"]}
 
+    # ---- validation phase: n_d (FP64 GMRES) and n_ir (GMRES-IR) for the penalty
+    valid = None
+    if not args.no_fp64:
+        from paper_2507_11512_gb300 import validation
+
+        def vsolve(prec, tol, maxit):
+            x.zero_()
+            inner = hpg.HPG_FP64 if prec == "fp64" else hpg.HPG_FP32
+            return hpg.gmres_ir_solve(prob.h, b, x, tol=tol, restart=w.restart, maxit=maxit,
+                                      inner=inner,
+                                      basis=basis_mxp if inner == hpg.HPG_FP32 else inner)
+        valid = validation.validate(vsolve, args.validation, w.tol, args.nd_max)
+
     # ---- per-kernel profile of one MxP solve (CUDA events on the solve's stream)
     hpg.set_profiling(prob.h, True)
     solve(hpg.HPG_FP32)
@@ -401,8 +418,8 @@ def run_gpu(args):
             "speedup_vs_fp64": (gflops / fp64["value"]) if fp64 else None,
             "time_speedup_vs_fp64": (fp64["ms_per_solve"] / (ms_max / args.steps)) if fp64
             else None,
-            "penalized_value": gflops * metrics.penalty(fp64["iterations"], n_ir) if fp64
-            else None,
+            "penalized_value": gflops * valid["penalty"] if valid else None,
+            "validation": valid,
             "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_fl_sum / e2e_s_max / 1e9, "unit": "GFLOP/s",

@@ -1,0 +1,49 @@
+"""Validation phase (Sec. 3, full-scale mode of Sec. 3.3) with the library's
+FP64 GMRES and mixed-precision GMRES-IR."""
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2507_11512_gb300 as hpg  # noqa: E402
+from paper_2507_11512_gb300 import validation  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def solver(p, b, basis=hpg.HPG_FP32):
+    def solve(prec, tol, maxit):
+        x = torch.zeros_like(b)
+        inner = hpg.HPG_FP64 if prec == "fp64" else hpg.HPG_FP32
+        return hpg.gmres_ir_solve(p.h, b, x, tol=tol, restart=30, maxit=maxit, inner=inner,
+                                  basis=basis if inner == hpg.HPG_FP32 else inner)
+    return solve
+
+
+@pytest.mark.parametrize("basis", [hpg.HPG_FP32, hpg.HPG_BF16])
+def test_fullscale_validation_caps_fp64_and_matches_its_residual(basis):
+    dims = (24, 24, 24)
+    with hpg.Problem(*dims, beta=0.5) as p:
+        ones = torch.ones(24 ** 3, dtype=torch.float64, device="cuda")
+        b = p.to_natural(p.spmv(p.to_storage(ones)))
+        r = validation.validate(solver(p, b, basis), "fullscale", 1e-9, nd_max=12)
+    assert r["n_d"] == 12 and not r["fp64_converged"]
+    assert 1e-9 < r["tau"] < 1e-2
+    assert r["mxp_converged"] and r["mxp_rel_residual"] < r["tau"]
+    assert r["penalty"] == min(1.0, r["n_d"] / r["n_ir"])
+
+
+def test_standard_validation_on_the_16cube():
+    with hpg.Problem(16, 16, 16, beta=0.5) as p:
+        ones = torch.ones(4096, dtype=torch.float64, device="cuda")
+        b = p.to_natural(p.spmv(p.to_storage(ones)))
+        r = validation.validate(solver(p, b), "standard", 1e-9)
+    assert r["fp64_converged"] and r["mxp_converged"] and r["tau"] == 1e-9
+    assert 0.8 <= r["penalty"] <= 1.0
