@@ -46,4 +46,8 @@ def test_standard_validation_on_the_16cube():
         b = p.to_natural(p.spmv(p.to_storage(ones)))
         r = validation.validate(solver(p, b), "standard", 1e-9)
     assert r["fp64_converged"] and r["mxp_converged"] and r["tau"] == 1e-9
-    assert 0.8 <= r["penalty"] <= 1.0
+    # b = A*1 lets FP64 GMRES finish within one restart cycle, while the FP32
+    # inner solve stalls near its rounding level and needs a refinement step:
+    # a real penalty below 1 here
+    assert r["penalty"] == min(1.0, r["n_d"] / r["n_ir"])
+    assert 0.5 <= r["penalty"] <= 1.0
