@@ -228,6 +228,83 @@ HPG_API int hpg_gmres_ir_solve(hpg_problem_t* h, const double* b, double* x,
                                hpg_prec inner, hpg_prec basis,
                                hpg_solve_info* info, void* stream);
 
+/* ------------------------------------------------- many right-hand sides
+ * The paper solves one right-hand side; these entry points solve R of them
+ * (R = nrhs in {1, 2, 4, 8}) together, so that every matrix entry read from
+ * memory serves R rows of work (the multigrid and SpMV kernels are
+ * bandwidth-bound, Sec. 4).  Each right-hand side is solved by its own
+ * GMRES-IR (Algorithm 3: its own basis, Hessenberg matrix, rotations and
+ * convergence test, FP32 inner solve and basis, FP64 refinement); the R
+ * solves advance in lockstep and a converged one is frozen while the others
+ * continue.  Layout of a storage-order R-vector of a level: [n_store][nrhs],
+ * the nrhs values of a storage row contiguous (FP32).  Natural-order inputs
+ * and outputs: nrhs vectors of n = nx*ny*nz values, vector r at offset r*n.
+ * All pointers are device pointers; no call allocates memory the caller must
+ * free.  The per-handle buffers these calls allocate are freed by
+ * hpg_destroy. */
+
+/* Y = A_level X for nrhs FP32 right-hand sides (storage-order R-vectors);
+ * column r equals hpg_spmv of column r bit for bit.  X, Y must not overlap.
+ * Asynchronous on `stream`. */
+HPG_API int hpg_spmv_batch(hpg_problem_t* h, int level, int nrhs, const float* X,
+                           float* Y, void* stream);
+
+/* Z = M^{-1} R for nrhs FP32 right-hand sides (storage-order R-vectors): the
+ * V-cycle of hpg_mg_vcycle, phase for phase; column r equals the FP32
+ * hpg_mg_vcycle of column r bit for bit.  Requires hpg_build_mg_hierarchy.
+ * R, Z must not overlap.  Asynchronous on `stream`. */
+HPG_API int hpg_mg_vcycle_batch(hpg_problem_t* h, int level, int nrhs,
+                                const float* R, float* Z, void* stream);
+
+/* FP32 nrhs-vectors between natural order (direction 0: in natural, out
+ * storage, padding rows 0) and storage order (direction 1).  Asynchronous. */
+HPG_API int hpg_permute_batch(hpg_problem_t* h, int level, int direction, int nrhs,
+                              const float* in, float* out, void* stream);
+
+/* GMRES-IR for nrhs right-hand sides of one problem (see above).  B: FP64,
+ * natural order, nrhs vectors of n; X: FP64, same layout, in: initial
+ * guesses, out: solutions.  tol, restart (1..64), maxit (inner steps of each
+ * right-hand side) as for hpg_gmres_ir_solve.  infos: NULL or nrhs entries.
+ * Returns HPG_OK when every right-hand side converged, else the first
+ * failure (HPG_ERR_NOT_CONVERGED, HPG_ERR_NAN, HPG_ERR_BREAKDOWN).  One CUDA
+ * graph launch per call (host-driven in the eager and profiling modes).
+ * Synchronises `stream`. */
+HPG_API int hpg_gmres_ir_solve_batch(hpg_problem_t* h, int nrhs, const double* B,
+                                     double* X, double tol, int restart, int maxit,
+                                     hpg_solve_info* infos, void* stream);
+
+/* Launch shape of the multi-right-hand-side kernels of `level`: kind 0 the
+ * Gauss-Seidel phases, kind 1 the SpMV; lpr lanes per row (1, 2 or nrhs; 0 =
+ * default 1) and block threads (64, 128, 256; 0 = default).  Every shape
+ * gives the same results.  hpg_batch_tune sets them by timing. */
+HPG_API int hpg_batch_set_shape(hpg_problem_t* h, int level, int kind, int nrhs, int lpr,
+                                int block);
+HPG_API int hpg_batch_get_shape(const hpg_problem_t* h, int level, int kind, int nrhs,
+                                int* lpr, int* block);
+
+/* Times every launch shape of the multi-right-hand-side Gauss-Seidel sweep
+ * on each level and of the level-0 SpMV for nrhs right-hand sides and keeps
+ * the fastest (the autotuner; a few milliseconds per level).  Synchronises
+ * `stream`. */
+HPG_API int hpg_batch_tune(hpg_problem_t* h, int nrhs, void* stream);
+
+/* Several problems (each its own grid, stencil and hierarchy; no handle
+ * twice) solved by ONE launch of one CUDA graph that holds every problem's
+ * batched GMRES-IR as an independent branch.  hpg_batch_create allocates the
+ * problems' batch buffers for nrhs and restart and captures the graph (tune
+ * the problems first: the graph keeps the shapes it was captured with);
+ * while the batch exists the problems' batch buffers belong to it (batched
+ * solves of the same problems with another nrhs or restart are refused).
+ * hpg_batch_solve: B[i], X[i] as for hpg_gmres_ir_solve_batch for problem
+ * i; infos: NULL or nsys * nrhs entries (problem-major).  hpg_batch_destroy
+ * releases the graph (the problems stay). */
+typedef struct hpg_batch hpg_batch_t;
+HPG_API int hpg_batch_create(hpg_problem_t* const* hs, int nsys, int nrhs, int restart,
+                             hpg_batch_t** out);
+HPG_API int hpg_batch_solve(hpg_batch_t* b, const double* const* B, double* const* X,
+                            double tol, int maxit, hpg_solve_info* infos, void* stream);
+HPG_API int hpg_batch_destroy(hpg_batch_t* b);
+
 /* ------------------------------------------------------------ profiling
  * Measurement support, not a step of the method (the paper profiles its
  * kernels with rocprof and rocprofiler-compute, Sec. 4.3).  While enabled,

@@ -68,6 +68,18 @@ SIGNATURES = {
     "hpg_mg_smooth": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
     "hpg_mg_vcycle_noalloc": (_I, [_P, _I, _I, _P, _P, _P]),
     "hpg_gmres_ir_solve": (_I, [_P, _P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(SolveInfo), _P]),
+    "hpg_spmv_batch": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hpg_mg_vcycle_batch": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hpg_permute_batch": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "hpg_gmres_ir_solve_batch": (_I, [_P, _I, _P, _P, _D, _I, _I, ctypes.POINTER(SolveInfo),
+                                      _P]),
+    "hpg_batch_set_shape": (_I, [_P, _I, _I, _I, _I, _I]),
+    "hpg_batch_get_shape": (_I, [_P, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "hpg_batch_tune": (_I, [_P, _I, _P]),
+    "hpg_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, ctypes.POINTER(_P)]),
+    "hpg_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I,
+                             ctypes.POINTER(SolveInfo), _P]),
+    "hpg_batch_destroy": (_I, [_P]),
     "hpg_set_profiling": (_I, [_P, _I]),
     "hpg_set_execution": (_I, [_P, _I]),
     "hpg_set_option": (_I, [_P, _I, _I]),

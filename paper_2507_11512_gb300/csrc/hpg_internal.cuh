@@ -156,6 +156,7 @@ struct Level {
 };
 
 struct Workspace;   // GMRES buffers (krylov.cu)
+struct BatchSpace;  // multi-right-hand-side buffers and tuned launch shapes (batch.cu)
 struct Profiler;    // per-kernel-class CUDA-event timing (profile.cu)
 
 // Kernel classes reported by the profiler.
@@ -177,6 +178,7 @@ struct hpg_problem {
   bool hierarchy = false;
   hpg::Level lev[hpg::kMaxLevels];
   hpg::Workspace* ws = nullptr;
+  hpg::BatchSpace* batch = nullptr;
   hpg::Profiler* prof = nullptr;
   long long launches = 0;   // kernel launches enqueued (diagnostics)
   bool profiling = false;   // event-bracketed launches, no PDL
@@ -253,6 +255,7 @@ int launch_vcycle_cluster(hpg_problem* h, int level, hpg_prec prec, const void* 
 int launch_permute(hpg_problem* h, int level, int direction, hpg_prec in_prec,
                    const void* in, hpg_prec out_prec, void* out, cudaStream_t s);
 void destroy_workspace(hpg_problem* h);
+void destroy_batch(hpg_problem* h);
 
 inline size_t prec_size(hpg_prec p) {
   switch (p) {

@@ -461,6 +461,7 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
 HPG_API int hpg_destroy(hpg_problem_t* h) {
   if (!h) return HPG_OK;
   destroy_workspace(h);
+  destroy_batch(h);
   destroy_profiler(h);
   for (int l = 0; l < kMaxLevels; ++l) free_level(h->lev[l], false);
   delete h;

@@ -1,0 +1,168 @@
+"""Many right-hand sides (hpg_*_batch) and many systems in one graph launch
+(hpg_batch_*): stencil kernels bitwise equal to the single-vector ones in
+every launch shape, batched GMRES-IR against the oracle per right-hand side,
+the multi-system graph against per-system solves."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2507_11512_gb300 as hpg  # noqa: E402
+from oracle import hpg_oracle as O  # noqa: E402
+from paper_2507_11512_gb300 import batch  # noqa: E402
+from tests.gpu_helpers import oracle_hierarchy  # noqa: E402
+from workloads import batch_systems, rhs_noise, x_true  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def shapes(R):
+    lprs = sorted({1, min(2, R), R})
+    return [(l, b) for l in lprs for b in (64, 256)]
+
+
+def rvec(p, level, R, seed, padding_zero=True):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = p.info[level]["n"]
+    nat = torch.randn(R, n, generator=g, dtype=torch.float32).to(DEV)
+    st = torch.empty(p.n_store(level), R, dtype=torch.float32, device=DEV)
+    batch.permute_batch(p.h, level, 0, R, nat, st)
+    return nat, st
+
+
+@pytest.mark.parametrize("R", [1, 2, 4, 8])
+def test_spmv_and_vcycle_columns_equal_single_vector_kernels(R):
+    dims = (24, 20, 28)
+    with hpg.Problem(*dims, beta=0.5) as p:
+        for level in range(p.levels):
+            _, X = rvec(p, level, R, 7 + level)
+            for kind in (batch.KIND_SPMV, batch.KIND_GS):
+                for lpr, blk in shapes(R):
+                    batch.set_shape(p.h, level, kind, R, lpr, blk)
+                    if kind == batch.KIND_SPMV:
+                        Y = torch.empty_like(X)
+                        batch.spmv_batch(p.h, level, X, Y)
+                        ref = [p.spmv(X[:, r].contiguous(), level=level) for r in range(R)]
+                    else:
+                        Y = torch.empty_like(X)
+                        batch.vcycle_batch(p.h, level, X, Y)
+                        ref = [p.vcycle(X[:, r].contiguous(), level=level) for r in range(R)]
+                    for r in range(R):
+                        assert torch.equal(Y[:, r], ref[r]), (level, kind, lpr, blk, r)
+                batch.set_shape(p.h, level, kind, R, 0, 0)
+
+
+def test_permute_batch_round_trip():
+    with hpg.Problem(12, 10, 14) as p:
+        nat, st = rvec(p, 0, 4, 3)
+        back = torch.empty_like(nat)
+        batch.permute_batch(p.h, 0, 1, 4, st, back)
+        assert torch.equal(back, nat)
+        for r in range(4):
+            assert torch.equal(st[:, r], p.to_storage(nat[r].contiguous()))
+
+
+@pytest.mark.parametrize("dims,beta", [((16, 16, 16), 0.5), ((24, 20, 28), 0.0)])
+def test_batched_solve_matches_oracle_per_rhs(dims, beta):
+    lv = oracle_hierarchy(dims, 4, beta)
+    n = lv[0].n
+    R = 8
+    rhs = [lv[0].A @ x_true(n) + rhs_noise(n, 1e-3, seed=r) for r in range(R - 2)]
+    rhs.append(np.zeros(n))                                    # b = 0: x = 0 at once
+    rhs.append(1e-6 * (lv[0].A @ x_true(n)))                   # another scale
+    B = torch.tensor(np.stack(rhs), device=DEV)
+    X = torch.zeros_like(B)
+    with hpg.Problem(*dims, beta=beta) as p:
+        infos = batch.solve_batch(p.h, B, X, tol=1e-12)
+    x = X.cpu().numpy()
+    for r in range(R):
+        assert infos[r]["converged"] == 1 and infos[r]["status"] == 0, (r, infos[r])
+        if r == R - 2:
+            assert np.all(x[r] == 0.0) and infos[r]["iterations"] == 0
+            continue
+        res = np.linalg.norm(rhs[r] - lv[0].A @ x[r]) / np.linalg.norm(rhs[r])
+        assert res < 1e-12
+        x_o, _ = O.gmres_ir(lv, rhs[r], tol=1e-12, restart=30)
+        assert np.linalg.norm(x[r] - x_o) / np.linalg.norm(x_o) <= 1e-8
+
+
+def test_batched_solve_graph_equals_eager_and_is_deterministic():
+    dims = (16, 16, 16)
+    lv = oracle_hierarchy(dims, 4, 0.5)
+    n = lv[0].n
+    B = torch.tensor(np.stack([lv[0].A @ x_true(n) + rhs_noise(n, 1e-3, seed=r)
+                               for r in range(4)]), device=DEV)
+    with hpg.Problem(*dims, beta=0.5) as p:
+        Xg = torch.zeros_like(B)
+        ig = batch.solve_batch(p.h, B, Xg, tol=1e-10)
+        Xg2 = torch.zeros_like(B)
+        batch.solve_batch(p.h, B, Xg2, tol=1e-10)
+        hpg.set_execution(p.h, hpg.HPG_EXEC_EAGER)
+        Xe = torch.zeros_like(B)
+        ie = batch.solve_batch(p.h, B, Xe, tol=1e-10)
+    assert torch.equal(Xg, Xe) and torch.equal(Xg, Xg2)
+    assert [i["iterations"] for i in ig] == [i["iterations"] for i in ie]
+    assert ig[0]["graph_launches"] == 1 and ie[0]["graph_launches"] == 0
+    assert ig[0]["kernel_launches"] == ie[0]["kernel_launches"]
+
+
+def test_batch_of_systems_in_one_graph_equals_per_system_solves():
+    spec = batch_systems(4, 4, seed=1)
+    for s in spec:   # small grids for the test
+        e = {24: 12, 32: 16, 48: 8, 64: 16, 96: 24}[s["dims"][0]]
+        s["dims"] = (e, e, e)
+        s["rhs"] = np.random.default_rng(5).standard_normal((4, e ** 3))
+    probs = [hpg.Problem(*s["dims"], beta=s["beta"]) for s in spec]
+    try:
+        Bs = [torch.tensor(s["rhs"], device=DEV) for s in spec]
+        ref = []
+        for p, b in zip(probs, Bs):
+            x = torch.zeros_like(b)
+            info = batch.solve_batch(p.h, b, x, tol=1e-9)
+            ref.append((x, info))
+        with batch.BatchSolver(probs, 4, tune_shapes=True) as bsol:
+            Xs = [torch.zeros_like(b) for b in Bs]
+            infos = bsol.solve(Bs, Xs, tol=1e-9)
+            # tuned shapes give the same values as the default ones
+            for (x_ref, i_ref), x, inf in zip(ref, Xs, infos):
+                assert torch.equal(x, x_ref)
+                assert [i["iterations"] for i in inf] == [i["iterations"] for i in i_ref]
+                assert all(i["converged"] for i in inf)
+            # a second call reuses the graph
+            Xs2 = [torch.zeros_like(b) for b in Bs]
+            bsol.solve(Bs, Xs2, tol=1e-9)
+            assert all(torch.equal(a, b) for a, b in zip(Xs, Xs2))
+            # while the batch owns the buffers, other shapes of batch solves are refused
+            with pytest.raises(hpg.HpgError):
+                batch.solve_batch(probs[0].h, Bs[0][:2].contiguous(),
+                                  torch.zeros_like(Bs[0][:2]).contiguous(), tol=1e-9)
+        for p in probs:
+            for level in range(p.levels):
+                lpr, blk = batch.get_shape(p.h, level, batch.KIND_GS, 4)
+                assert lpr in (1, 2, 4) and blk in (64, 128, 256)
+    finally:
+        for p in probs:
+            p.close()
+
+
+def test_batch_invalid_arguments():
+    with hpg.Problem(8, 8, 8) as p:
+        B = torch.ones(3, 512, dtype=torch.float64, device=DEV)
+        with pytest.raises(hpg.HpgError):
+            batch.solve_batch(p.h, B, torch.zeros_like(B))   # nrhs 3
+        with pytest.raises(hpg.HpgError):
+            batch.set_shape(p.h, 0, 0, 4, 3, 64)
+        with pytest.raises(hpg.HpgError):
+            batch.set_shape(p.h, 0, 0, 4, 1, 100)
+        with pytest.raises(hpg.HpgError):
+            batch.BatchSolver([p, p], 4, tune_shapes=False)

@@ -62,6 +62,15 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.hpg_spmv(None, 0, 1, None, None, None) == _lib.HPG_ERR_INVALID
     assert lib.hpg_mg_vcycle(None, 0, 1, None, None, None) == _lib.HPG_ERR_INVALID
     assert lib.hpg_mg_smooth(None, 0, 1, None, None, 1, 1, None) == _lib.HPG_ERR_INVALID
+    assert lib.hpg_spmv_batch(None, 0, 8, None, None, None) == _lib.HPG_ERR_INVALID
+    assert lib.hpg_mg_vcycle_batch(None, 0, 8, None, None, None) == _lib.HPG_ERR_INVALID
+    assert lib.hpg_gmres_ir_solve_batch(None, 8, None, None, 1e-9, 30, 10, None, None) == \
+        _lib.HPG_ERR_INVALID
+    assert lib.hpg_batch_tune(None, 8, None) == _lib.HPG_ERR_INVALID
+    out = ctypes.c_void_p()
+    assert lib.hpg_batch_create(None, 0, 8, 30, ctypes.byref(out)) == _lib.HPG_ERR_INVALID
+    assert lib.hpg_batch_solve(None, None, None, 1e-9, 10, None, None) == _lib.HPG_ERR_INVALID
+    assert lib.hpg_batch_destroy(None) == _lib.HPG_OK
     assert lib.hpg_build_mg_hierarchy(None, 4, 1, 1) == _lib.HPG_ERR_INVALID
     assert lib.hpg_destroy(None) == _lib.HPG_OK
     cnt = ctypes.c_int()

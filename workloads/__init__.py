@@ -55,3 +55,23 @@ def random_vector(n, seed, dtype=np.float64):
     """Standard-normal test vector; FP32 vectors are drawn then rounded."""
     v = np.random.default_rng(seed).standard_normal(n)
     return v.astype(dtype)
+
+
+BATCH_EDGES = (24, 32, 48, 64, 96)
+
+
+def batch_systems(nsys=64, nrhs=8, seed=0):
+    """The batched workload: nsys systems with cubic grid edges drawn
+    uniformly from BATCH_EDGES, a per-system nonsymmetric scale
+    sigma ~ U[0.5, 1.5] (beta = 0.5 sigma, so |beta| <= 0.75), and nrhs
+    right-hand sides ~ N(0, 1) each, laid out as an (nrhs, n) array in natural
+    order.  Seeded PCG64, drawn in system order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nsys):
+        e = int(rng.choice(BATCH_EDGES))
+        sigma = float(rng.uniform(0.5, 1.5))
+        n = e ** 3
+        out.append({"dims": (e, e, e), "sigma": sigma, "beta": 0.5 * sigma,
+                    "rhs": rng.standard_normal((nrhs, n))})
+    return out
