@@ -305,6 +305,17 @@ HPG_API int hpg_batch_solve(hpg_batch_t* b, const double* const* B, double* cons
                             double tol, int maxit, hpg_solve_info* infos, void* stream);
 HPG_API int hpg_batch_destroy(hpg_batch_t* b);
 
+/* Autotuner of a batch: lanes per row (1, 2 or nrhs) of the
+ * multi-right-hand-side kernels chosen by timing whole batch solves of B from
+ * x0 = 0 (X as for hpg_batch_solve, overwritten) with each candidate applied to
+ * every problem and level, then the graph is recaptured with the fastest.
+ * Under a batch the problems' kernels run concurrently, so the per-problem
+ * timing of hpg_batch_tune does not predict it.  times_ms: NULL or 3 floats,
+ * the measured solve times of lanes per row 1, 2, nrhs (fewer for nrhs < 4).
+ * Synchronises `stream`. */
+HPG_API int hpg_batch_tune_solve(hpg_batch_t* b, const double* const* B, double* const* X,
+                                 double tol, int maxit, float* times_ms, void* stream);
+
 /* ------------------------------------------------------------ profiling
  * Measurement support, not a step of the method (the paper profiles its
  * kernels with rocprof and rocprofiler-compute, Sec. 4.3).  While enabled,

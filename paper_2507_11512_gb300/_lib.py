@@ -80,6 +80,8 @@ SIGNATURES = {
     "hpg_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I,
                              ctypes.POINTER(SolveInfo), _P]),
     "hpg_batch_destroy": (_I, [_P]),
+    "hpg_batch_tune_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I,
+                                  ctypes.POINTER(ctypes.c_float), _P]),
     "hpg_set_profiling": (_I, [_P, _I]),
     "hpg_set_execution": (_I, [_P, _I]),
     "hpg_set_option": (_I, [_P, _I, _I]),

@@ -74,7 +74,9 @@ def tune(h, nrhs, stream=None):
 class BatchSolver:
     """Several Problems solved by one CUDA graph launch (hpg_batch_*)."""
 
-    def __init__(self, problems, nrhs, restart=30, tune_shapes=True):
+    def __init__(self, problems, nrhs, restart=30, tune_shapes=False):
+        """tune_shapes: per-problem isolated tuning (hpg_batch_tune) before the
+        capture; for the batch itself prefer tune(), which times the batch."""
         self.problems = list(problems)
         self.nrhs = nrhs
         self.restart = restart
@@ -97,6 +99,18 @@ class BatchSolver:
             raise HpgError(st, "hpg_batch_solve")
         d = [i.as_dict() for i in infos]
         return [d[i * self.nrhs:(i + 1) * self.nrhs] for i in range(n)]
+
+    def tune(self, Bs, Xs, tol=1e-9, maxit=10000, stream=None):
+        """hpg_batch_tune_solve: times whole batch solves of (Bs, Xs) per
+        candidate launch shape and keeps the fastest (Xs is overwritten)."""
+        n = len(self.problems)
+        bp = (ctypes.c_void_p * n)(*[_ptr(b) for b in Bs])
+        xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in Xs])
+        times = (ctypes.c_float * 3)()
+        check(load().hpg_batch_tune_solve(self.b, bp, xp, tol, maxit, times, _stream(stream)),
+              "hpg_batch_tune_solve")
+        cand = sorted({1, min(2, self.nrhs), self.nrhs})
+        return dict(zip(cand, list(times)[:len(cand)]))
 
     def close(self):
         if self.b:
@@ -140,8 +154,12 @@ def main(argv=None):
     Xs = [torch.zeros_like(b) for b in Bs]
     setup_s = time.perf_counter() - t0
     t1 = time.perf_counter()
-    solver = BatchSolver(probs, a.nrhs, tune_shapes=not a.no_tune)
+    solver = BatchSolver(probs, a.nrhs)
+    tune_ms = None
+    if not a.no_tune:
+        tune_ms = solver.tune(Bs, Xs, tol=a.tol)
     create_s = time.perf_counter() - t1
+    shape = get_shape(probs[0].h, 0, KIND_GS, a.nrhs)
     times, infos = [], None
     for it in range(a.reps + 1):
         for x in Xs:
@@ -170,7 +188,8 @@ def main(argv=None):
         "ms_per_batch_solve": ms, "gflops": flops / (ms / 1e3) / 1e9,
         "rhs_solved_per_s": a.systems * a.nrhs / (ms / 1e3),
         "iterations_min_median_max": [min(its), sorted(its)[len(its) // 2], max(its)],
-        "setup_s": setup_s, "tune_and_capture_s": create_s, "tuned": not a.no_tune}))
+        "setup_s": setup_s, "tune_and_capture_s": create_s, "tuned": not a.no_tune,
+        "lanes_per_row": shape[0], "tuning_solve_ms_by_lanes_per_row": tune_ms}))
     solver.close()
     for p in probs:
         p.close()

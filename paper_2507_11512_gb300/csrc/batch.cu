@@ -1454,6 +1454,27 @@ static void free_batch(hpg_batch* b) {
   delete b;
 }
 
+// (Re)captures the batch graph with the problems' current launch shapes.
+static int capture_batch_graph(hpg_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  cudaGraph_t G = nullptr;
+  HPG_CK(cudaGraphCreate(&G, 0));
+  int rc = HPG_OK;
+  for (size_t i = 0; i < b->hs.size() && rc == HPG_OK; ++i)
+    rc = capture_msolve_r(b->hs[i], b->nrhs, b->restart, G, b->hk[i]);
+  if (rc) return rc;   // a failed capture's graph is abandoned, not destroyed
+  cudaError_t e = cudaGraphInstantiate(&b->exec, G, 0);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate(batch)", __FILE__, __LINE__);
+  }
+  b->graph = G;
+  return HPG_OK;
+}
+
 template <int R>
 static int batch_prepare(hpg_problem* h, const double* B, const double* X, double tol, int m,
                          int maxit, cudaStream_t s) {
@@ -1513,21 +1534,8 @@ HPG_API int hpg_batch_create(hpg_problem_t* const* hs, int nsys, int nrhs, int r
       if (rc == HPG_OK) b->hk.push_back(hk);
     }
   }
-  if (rc == HPG_OK) {
-    cudaError_t e = cudaGraphCreate(&b->graph, 0);
-    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphCreate(batch)", __FILE__, __LINE__);
-  }
-  for (int i = 0; i < nsys && rc == HPG_OK; ++i)
-    rc = capture_msolve_r(hs[i], nrhs, restart, b->graph, b->hk[i]);
-  if (rc == HPG_OK) {
-    cudaError_t e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-    if (e != cudaSuccess) {
-      b->exec = nullptr;
-      rc = cuda_fail(e, "cudaGraphInstantiate(batch)", __FILE__, __LINE__);
-    }
-  }
+  if (rc == HPG_OK) rc = capture_batch_graph(b);
   if (rc) {
-    if (b->graph && !b->exec) b->graph = nullptr;   // a failed capture's graph is abandoned
     free_batch(b);
     return rc;
   }
@@ -1578,6 +1586,70 @@ HPG_API int hpg_batch_solve(hpg_batch_t* b, const double* const* B, double* cons
     if (si != HPG_OK && (status == HPG_OK || status == HPG_ERR_NOT_CONVERGED)) status = si;
   }
   return status;
+}
+
+HPG_API int hpg_batch_tune_solve(hpg_batch_t* b, const double* const* B, double* const* X,
+                                 double tol, int maxit, float* times_ms, void* stream) {
+  if (!b || !B || !X || !(tol > 0.0) || maxit < 0) {
+    set_error("hpg_batch_tune_solve: invalid argument");
+    return HPG_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int R = b->nrhs;
+  std::vector<int> lprs = {1};
+  if (R >= 2) lprs.push_back(2);
+  if (R > 2) lprs.push_back(R);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HPG_CK(cudaEventCreate(&e0));
+  HPG_CK(cudaEventCreate(&e1));
+  auto set_all = [&](int lpr) {
+    for (hpg_problem* h : b->hs) {
+      BatchSpace* bs = h->batch;
+      for (int l = 0; l < h->nlev; ++l)
+        for (int kind = 0; kind < 2; ++kind) bs->shape[l][kind][R] = Shape{lpr, 0};
+    }
+  };
+  int rc = HPG_OK;
+  float best = 1e30f;
+  int best_lpr = 1;
+  // one untimed solve first (lazy module loading, first-touch of buffers)
+  for (int pass = 0; pass <= (int)lprs.size() && rc == HPG_OK; ++pass) {
+    const int lpr = lprs[pass == 0 ? 0 : pass - 1];
+    set_all(lpr);
+    rc = capture_batch_graph(b);
+    if (rc) break;
+    for (size_t i = 0; i < b->hs.size() && rc == HPG_OK; ++i) {   // every solve from x0 = 0
+      const Level& L0 = b->hs[i]->lev[0];
+      if (cudaMemsetAsync(X[i], 0, sizeof(double) * L0.n * R, s) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync(batch tuning x0)", __FILE__, __LINE__);
+    }
+    if (rc) break;
+    if (cudaEventRecord(e0, s) != cudaSuccess) {
+      rc = HPG_ERR_CUDA;
+      break;
+    }
+    const int st = hpg_batch_solve(b, B, X, tol, maxit, nullptr, stream);
+    if (st != HPG_OK && st != HPG_ERR_NOT_CONVERGED) {
+      rc = st;
+      break;
+    }
+    float ms = 0.0f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "batch tuning events", __FILE__, __LINE__);
+      break;
+    }
+    if (pass > 0 && times_ms) times_ms[pass - 1] = ms;
+    if (pass > 0 && ms < best) {
+      best = ms;
+      best_lpr = lpr;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  set_all(best_lpr);
+  return capture_batch_graph(b);
 }
 
 HPG_API int hpg_batch_destroy(hpg_batch_t* b) {

@@ -132,6 +132,8 @@ def test_batch_of_systems_in_one_graph_equals_per_system_solves():
             ref.append((x, info))
         with batch.BatchSolver(probs, 4, tune_shapes=True) as bsol:
             Xs = [torch.zeros_like(b) for b in Bs]
+            bsol.tune(Bs, Xs, tol=1e-9)
+            Xs = [torch.zeros_like(b) for b in Bs]
             infos = bsol.solve(Bs, Xs, tol=1e-9)
             # tuned shapes give the same values as the default ones
             for (x_ref, i_ref), x, inf in zip(ref, Xs, infos):

@@ -70,6 +70,7 @@ def test_host_side_validation_without_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.hpg_batch_create(None, 0, 8, 30, ctypes.byref(out)) == _lib.HPG_ERR_INVALID
     assert lib.hpg_batch_solve(None, None, None, 1e-9, 10, None, None) == _lib.HPG_ERR_INVALID
+    assert lib.hpg_batch_tune_solve(None, None, None, 1e-9, 10, None, None) == _lib.HPG_ERR_INVALID
     assert lib.hpg_batch_destroy(None) == _lib.HPG_OK
     assert lib.hpg_build_mg_hierarchy(None, 4, 1, 1) == _lib.HPG_ERR_INVALID
     assert lib.hpg_destroy(None) == _lib.HPG_OK
