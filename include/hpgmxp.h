@@ -358,10 +358,18 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
  * as one kernel on one thread-block cluster (up to 16 CTAs, hardware cluster
  * barrier between colour phases); 0: one kernel launch per colour phase /
  * transfer on every level.  HPG_OPT_PDL (default 1): programmatic dependent
- * launch between the solve's kernels.  Setting an option drops captured solve
- * graphs.  HPG_ERR_INVALID for an unknown option. */
+ * launch between the solve's kernels.  HPG_OPT_GS_PIPELINE: on levels whose
+ * matrix streams from memory, a symmetric Gauss-Seidel sweep may run as one
+ * kernel in which a tile of a colour phase starts as soon as the tiles of the
+ * previous phase within one grid plane of it are done (bounded waits; a wait
+ * that runs out makes the solve return HPG_ERR_TIMEOUT) instead of one launch
+ * per colour phase; same results.  0: never; 1 (default): FP64 sweeps only
+ * (measured faster on GB300 for FP64, slower for FP32); 2: always.  Setting
+ * an option drops captured solve graphs.
+ * HPG_ERR_INVALID for an unknown option. */
 #define HPG_OPT_COARSE_CLUSTER 1
 #define HPG_OPT_PDL 2
+#define HPG_OPT_GS_PIPELINE 3
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);
 
 /* Frees everything the handle owns (NULL is accepted). */

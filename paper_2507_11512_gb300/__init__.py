@@ -12,7 +12,7 @@ import ctypes
 from ._lib import (HPG_BF16, HPG_ERR_ALLOC, HPG_ERR_BREAKDOWN, HPG_ERR_CUDA,  # noqa: F401
                    HPG_ERR_INVALID, HPG_ERR_NAN, HPG_ERR_NOT_CONVERGED, HPG_ERR_STATE,
                    HPG_ERR_UNSUPPORTED, HPG_EXEC_EAGER, HPG_EXEC_GRAPH, HPG_FP16, HPG_FP32,
-                   HPG_FP64, HPG_OK, HPG_OPT_COARSE_CLUSTER, HPG_OPT_PDL, HpgError,
+                   HPG_FP64, HPG_OK, HPG_OPT_COARSE_CLUSTER, HPG_OPT_GS_PIPELINE, HPG_OPT_PDL, HpgError,
                    KernelStat, LevelDesc, SolveInfo, StencilParams, check, load)
 
 __all__ = ["setup_problem", "build_mg_hierarchy", "num_levels", "level_info", "permute",
@@ -152,7 +152,8 @@ def set_execution(h, mode):
 
 
 def set_option(h, option, value):
-    """hpg_set_option: HPG_OPT_COARSE_CLUSTER or HPG_OPT_PDL, 0 / 1."""
+    """hpg_set_option: HPG_OPT_COARSE_CLUSTER, HPG_OPT_PDL (0 / 1) or
+    HPG_OPT_GS_PIPELINE (0 never, 1 FP64 sweeps, 2 always)."""
     check(load().hpg_set_option(h, option, int(value)), "hpg_set_option")
 
 

@@ -153,7 +153,17 @@ struct Level {
   // correction; every level: scratch), per precision: [0] FP64, [1] FP32.
   void* rhs[2] = {nullptr, nullptr};
   void* sol[2] = {nullptr, nullptr};
+  // pipelined symmetric sweep (streamed levels): per-tile completion flags
+  // [kMaxPipePhases][pipe_tiles] and the sweep's control words
+  // (kPipeQueue, kPipeFinish, kPipeEpoch, kPipeAbort)
+  int* pipe_flags = nullptr;
+  unsigned* pipe_sync = nullptr;
+  int pipe_tiles = 0;
 };
+
+constexpr int kPipeTileRows = 256;   // rows of one tile (= threads of its CTA)
+constexpr int kMaxPipePhases = 16;   // colour phases of one symmetric sweep (15 used)
+enum PipeWord { kPipeQueue = 0, kPipeFinish = 1, kPipeEpoch = 2, kPipeAbort = 3, kPipeWords = 4 };
 
 struct Workspace;   // GMRES buffers (krylov.cu)
 struct BatchSpace;  // multi-right-hand-side buffers and tuned launch shapes (batch.cu)
@@ -186,6 +196,9 @@ struct hpg_problem {
   bool pdl_enabled = true;  // programmatic dependent launch on the chain
   bool pdl_next = false;    // the previous stream operation was a kernel
   bool coarse_cluster = false;    // coarse levels of a V-cycle in one cluster kernel
+  int gs_pipeline = 1;            // streamed levels, pipelined sweep kernel: 0 never,
+                                  // 1 FP64 sweeps only (measured faster there), 2 always
+  unsigned* pipe_err = nullptr;   // device word: a pipelined sweep's wait ran out
   int vc_cluster[2] = {0, 0};     // its cluster size per precision (0: not probed, <0: none)
 };
 

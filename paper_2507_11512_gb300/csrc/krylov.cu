@@ -760,7 +760,8 @@ norm2_kernel(const double* __restrict__ v, long long ns, double* __restrict__ pa
 // ||r|| / ||b|| < tol ends the solve; so do a recorded breakdown / NaN and
 // maxit.  In graph mode it sets the WHILE node's condition.
 __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* st,
-                                   const int* __restrict__ dev_err, unsigned long long loop) {
+                                   const int* __restrict__ dev_err,
+                                   const unsigned* __restrict__ pipe_err, unsigned long long loop) {
   pdl_trigger();
   pdl_wait();
   if (threadIdx.x != 0) return;
@@ -769,7 +770,7 @@ __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* 
   st->rho = rho;
   st->rel = rel;
   bool done = true;
-  if (*dev_err != 0) {
+  if (*dev_err != 0 || (pipe_err && *pipe_err != 0)) {
     st->status = HPG_ERR_TIMEOUT;   // a kernel's bounded wait gave up
   } else if (!isfinite(rel)) {
     st->status = HPG_ERR_NAN;
@@ -980,7 +981,7 @@ static int enqueue_outer(hpg_problem* h, unsigned long long loop, cudaStream_t s
   if (rc) return rc;
   return launch(h, K_NORM, 0, HPG_FP64, 0.0, s, "outer_check_kernel", [&] {
     return kl(h, outer_check_kernel, 1, 32, s, (const double*)ws->rho2, ws->st,
-              (const int*)ws->dev_err, loop);
+              (const int*)ws->dev_err, (const unsigned*)h->pipe_err, loop);
   });
 }
 
@@ -1234,6 +1235,7 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
   const SolveState& fs = *ws->st_host;
   if (fs.status == HPG_ERR_TIMEOUT) {
     HPG_CK(cudaMemset(ws->dev_err, 0, 16));
+    if (h->pipe_err) HPG_CK(cudaMemset(h->pipe_err, 0, sizeof(unsigned) * 4));
     status = HPG_ERR_TIMEOUT;
     converged = false;
   }

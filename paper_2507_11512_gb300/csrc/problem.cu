@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 
 #include "hpg_internal.cuh"
@@ -202,6 +203,11 @@ static void free_level(Level& L, bool keep_matrix) {
     dev_free(L.sol[p]);
     L.rhs[p] = L.sol[p] = nullptr;
   }
+  dev_free(L.pipe_flags);
+  dev_free(L.pipe_sync);
+  L.pipe_flags = nullptr;
+  L.pipe_sync = nullptr;
+  L.pipe_tiles = 0;
   if (!keep_matrix) {
     dev_free(L.cols);
     dev_free(L.v32);
@@ -392,6 +398,17 @@ HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels, int pre_sweeps,
       if (rc == HPG_OK) rc = dev_alloc(&L.sol[pi], es * L.g.n_store);
     }
   }
+  // completion flags of the pipelined sweep on levels whose matrix streams
+  if (rc == HPG_OK && !h->pipe_err) rc = dev_alloc((void**)&h->pipe_err, sizeof(unsigned) * 4);
+  for (int l = 0; l < h->nlev && rc == HPG_OK; ++l) {
+    Level& L = h->lev[l];
+    if (L.g.n_store * 27LL * 8 <= kStreamMatrixBytes) continue;
+    long long maxrows = 0;
+    for (int c = 0; c < kColours; ++c) maxrows = std::max(maxrows, L.g.off[c + 1] - L.g.off[c]);
+    L.pipe_tiles = (int)((maxrows + kPipeTileRows - 1) / kPipeTileRows);
+    rc = dev_alloc((void**)&L.pipe_flags, sizeof(int) * (size_t)kMaxPipePhases * L.pipe_tiles);
+    if (rc == HPG_OK) rc = dev_alloc((void**)&L.pipe_sync, sizeof(unsigned) * kPipeWords);
+  }
   if (rc == HPG_OK) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = cuda_fail(e, "hierarchy build", __FILE__, __LINE__);
@@ -450,6 +467,13 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
   switch (option) {
     case HPG_OPT_COARSE_CLUSTER: h->coarse_cluster = value != 0; break;
     case HPG_OPT_PDL: h->pdl_enabled = value != 0; break;
+    case HPG_OPT_GS_PIPELINE:
+      if (value < 0 || value > 2) {
+        set_error("hpg_set_option: HPG_OPT_GS_PIPELINE takes 0, 1 or 2, not %d", value);
+        return HPG_ERR_INVALID;
+      }
+      h->gs_pipeline = value;
+      break;
     default:
       set_error("hpg_set_option: unknown option %d", option);
       return HPG_ERR_INVALID;
@@ -464,6 +488,7 @@ HPG_API int hpg_destroy(hpg_problem_t* h) {
   destroy_batch(h);
   destroy_profiler(h);
   for (int l = 0; l < kMaxLevels; ++l) free_level(h->lev[l], false);
+  dev_free(h->pipe_err);
   delete h;
   return HPG_OK;
 }

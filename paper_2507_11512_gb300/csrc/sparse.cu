@@ -7,6 +7,10 @@
 // contiguous, so a warp reads each slot of 32 consecutive rows as one 128-byte
 // (FP32) or 256-byte (FP64) transaction.
 
+#include <string.h>
+
+#include <algorithm>
+
 #include "hpg_internal.cuh"
 
 namespace hpg {
@@ -147,6 +151,161 @@ gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, 
   x[row] = acc / a[kCentre];
 }
 
+// ---------------------------------------------- pipelined symmetric sweep
+// One kernel runs all colour phases of a symmetric sweep (Sec. 3.2.1) on a
+// level whose matrix streams from memory.  The phases' rows are cut into
+// tiles of kPipeTileRows rows, handed out in phase order by an atomic queue.
+// A tile of phase p may start once the tiles of phase p-1 that cover the grid
+// planes K-1 .. K+1 of its own rows (k = 2K + parity: every neighbour of a
+// point of plane K lies in planes K-1..K+1 of any colour block) have
+// finished.  That covers the values it reads and the readers of the values it
+// overwrites, in phase p-1 directly and, because each of those tiles waited
+// for its own window, in every earlier phase.  Waits are bounded: a wait that
+// runs out sets the error and abort words, and every tile still queued is
+// then skipped (the sweep's values are garbage; the solve reports a timeout).
+// The queue is deterministic in what each row computes: every row sees the
+// same neighbour values as in the phase-by-phase sweep, so results are equal
+// bit for bit.  Gathers go through L2 (other CTAs of this kernel write z).
+struct PipePhase {
+  long long row0;        // first storage row of the colour block
+  long long nrows;       // rows of the block (padded)
+  long long valid_end;   // gathers at or above this row read zero (from-zero sweep)
+  long long cnt;         // grid points of the block (planes of cdx*cdy points)
+  long long plane;       // cdx * cdy of this block
+  unsigned mask;         // slots read (masked first sweep)
+  int masked;            // 1: first forward sweep from z = 0
+  int tile0;             // first queue index of the phase
+};
+struct PipePlan {
+  int nphases;
+  int total_tiles;
+  int tile_stride;       // flag row length (tiles of the largest block)
+  PipePhase ph[kMaxPipePhases];
+};
+
+constexpr unsigned kPipeWaitPolls = 1u << 21;   // about 0.2-0.4 s of 100 ns naps
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One row of a colour phase, arithmetic as gs_phase_kernel; gathers via L2.
+template <typename T, bool MASKED>
+__device__ __forceinline__ void pipe_row(const T* __restrict__ vals, const int* __restrict__ cols,
+                                         long long ns, const T* __restrict__ r, T* z,
+                                         long long row, long long valid_end, unsigned mask) {
+  T acc = r[row];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    if (s == kCentre) continue;
+    if (MASKED) {
+      const bool use = (mask >> s) & 1u;
+      T a = T(0);
+      int c = 0;
+      if (use) {
+        a = ld_matrix<true>(vals + s * ns + row);
+        c = ld_matrix<true>(cols + s * ns + row);
+      }
+      const T xv = (use && c < valid_end) ? __ldcg(z + c) : T(0);
+      acc = fma(-a, xv, acc);
+    } else {
+      const T a = ld_matrix<true>(vals + s * ns + row);
+      const int c = ld_matrix<true>(cols + s * ns + row);
+      const T xv = (c < valid_end) ? __ldcg(z + c) : T(0);
+      acc = fma(-a, xv, acc);
+    }
+  }
+  const T diag = ld_matrix<true>(vals + kCentre * ns + row);
+  z[row] = acc / diag;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPipeTileRows, 6)
+gs_pipeline_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
+                   const T* __restrict__ r, T* z, const __grid_constant__ PipePlan plan,
+                   int* flags, unsigned* sync, unsigned* err) {
+  __shared__ int s_tile;
+  __shared__ int s_abort;
+  pdl_trigger();
+  pdl_wait();
+  const int done_mark = (int)*(volatile unsigned*)(sync + kPipeEpoch) + 1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_tile = (int)atomicAdd(sync + kPipeQueue, 1u);
+      s_abort = (int)*(volatile unsigned*)(sync + kPipeAbort);
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= plan.total_tiles || s_abort) break;
+    int p = 0;
+    while (p + 1 < plan.nphases && tile >= plan.ph[p + 1].tile0) ++p;
+    const PipePhase& ph = plan.ph[p];
+    const int t = tile - ph.tile0;
+    const long long r0 = (long long)t * kPipeTileRows;
+    if (p > 0 && threadIdx.x < 32) {
+      // window of phase p-1: planes K0-1 .. K1+1 of its block
+      const PipePhase& pp = plan.ph[p - 1];
+      const long long P1 = min(ph.cnt, r0 + kPipeTileRows);
+      if (r0 < P1) {
+        const long long K0 = r0 / ph.plane, K1 = (P1 - 1) / ph.plane;
+        const long long lo = max(0LL, (K0 - 1) * pp.plane);
+        const long long hi = min(pp.nrows, (K1 + 2) * pp.plane);
+        const int tlo = (int)(lo / kPipeTileRows);
+        const int thi = (int)((hi + kPipeTileRows - 1) / kPipeTileRows);
+        const int* f = flags + (long long)(p - 1) * plan.tile_stride;
+        bool ok = false;
+        for (unsigned it = 0; it < kPipeWaitPolls; ++it) {
+          bool mine = true;
+          for (int q = tlo + (int)threadIdx.x; q < thi; q += 32)
+            mine = mine && ld_acquire(f + q) == done_mark;
+          if (__all_sync(0xffffffffu, mine)) {
+            ok = true;
+            break;
+          }
+          if (*(volatile unsigned*)(sync + kPipeAbort)) break;
+          __nanosleep(100);
+        }
+        if (!ok && threadIdx.x == 0) {
+          if (!*(volatile unsigned*)(sync + kPipeAbort)) atomicExch(err, 1u);
+          atomicExch(sync + kPipeAbort, 1u);
+          s_abort = 1;
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const long long lr = r0 + threadIdx.x;
+    if (lr < ph.nrows) {
+      if (ph.masked)
+        pipe_row<T, true>(vals, cols, ns, r, z, ph.row0 + lr, ph.valid_end, ph.mask);
+      else
+        pipe_row<T, false>(vals, cols, ns, r, z, ph.row0 + lr, ph.valid_end, ph.mask);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(flags + (long long)p * plan.tile_stride + t, done_mark);
+    }
+  }
+  // the last CTA out resets the queue and moves to the next epoch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(sync + kPipeFinish, 1u) == gridDim.x - 1) {
+      sync[kPipeQueue] = 0u;
+      sync[kPipeFinish] = 0u;
+      sync[kPipeAbort] = 0u;
+      atomicAdd(sync + kPipeEpoch, 1u);
+      __threadfence();
+    }
+  }
+}
+
 // Fused residual + injection restriction (Sec. 3.2.4, last equation):
 // rc_I = r_{f_c(I)} - sum_j A_{f_c(I) j} z_j for every coarse point I.  The
 // coarse-coincident fine points are exactly fine colour block 7, stored in the
@@ -278,10 +437,73 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                 });
 }
 
+// Resident CTAs of the pipelined sweep kernel (queried once per precision).
+template <typename T>
+static int pipeline_grid(hpg_problem* h) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs_pipeline_kernel<T>,
+                                                      kPipeTileRows, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  return per_sm * h->num_sms;
+}
+
+// One symmetric sweep as one pipelined kernel (levels with completion
+// flags): the phases the phase-by-phase sweep would launch, in its order and
+// with its skipping of a repeated colour.
+template <typename T>
+static int symgs_pipelined(hpg_problem* h, int level, const T* r, T* z, bool from_zero,
+                           SweepState& st, cudaStream_t s) {
+  const Level& L = h->lev[level];
+  PipePlan plan;
+  memset(&plan, 0, sizeof(plan));
+  plan.tile_stride = L.pipe_tiles;
+  double bytes = 0.0;
+  int tiles = 0;
+  auto add = [&](int c, bool fz) {
+    if (st.last == c) return;
+    st.last = c;
+    const long long nrows = L.g.off[c + 1] - L.g.off[c];
+    if (nrows == 0) return;
+    PipePhase& ph = plan.ph[plan.nphases++];
+    ph.row0 = L.g.off[c];
+    ph.nrows = nrows;
+    ph.valid_end = fz ? ph.row0 : L.g.n_store;
+    ph.plane = (long long)L.g.cdx[c] * L.g.cdy[c];
+    ph.cnt = ph.plane * L.g.cdz[c];
+    ph.mask = gs_slot_mask(c, fz);
+    ph.masked = fz ? 1 : 0;
+    ph.tile0 = tiles;
+    tiles += (int)((nrows + kPipeTileRows - 1) / kPipeTileRows);
+    const int nslots = __builtin_popcount(ph.mask) - 1;
+    bytes += L.cnt[c] * ((nslots + 1.0) * sizeof(T) + nslots * 4.0 +
+                         (2.0 + nslots / 26.0) * sizeof(T));
+  };
+  for (int c = 0; c < kColours; ++c) add(c, from_zero);
+  for (int c = kColours - 1; c >= 0; --c) add(c, false);
+  plan.total_tiles = tiles;
+  if (tiles == 0) return HPG_OK;
+  const int grid = std::min(pipeline_grid<T>(h), tiles);
+  return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32, bytes, s,
+                "gs_pipeline_kernel", [&] {
+                  h->pdl_next = false;
+                  return kl(h, gs_pipeline_kernel<T>, grid, kPipeTileRows, s, Prec<T>::vals(L),
+                            L.cols, L.g.n_store, r, z, plan, L.pipe_flags, L.pipe_sync,
+                            h->pipe_err);
+                });
+}
+
 // One symmetric Gauss-Seidel sweep (eqs. (1)-(2)): colours 0..7 then 7..0.
 template <typename T>
 static int symgs(hpg_problem* h, int level, const T* r, T* z, bool from_zero, SweepState& st,
                  cudaStream_t s) {
+  const bool pipe = h->gs_pipeline == 2 || (h->gs_pipeline == 1 && sizeof(T) == 8);
+  if (pipe && h->lev[level].pipe_flags && h->pipe_err)
+    return symgs_pipelined<T>(h, level, r, z, from_zero, st, s);
   int rc;
   for (int c = 0; c < kColours; ++c)
     if ((rc = gs_phase<T>(h, level, r, z, c, from_zero, st, s))) return rc;
