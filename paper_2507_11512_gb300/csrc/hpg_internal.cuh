@@ -196,8 +196,9 @@ struct hpg_problem {
   bool pdl_enabled = true;  // programmatic dependent launch on the chain
   bool pdl_next = false;    // the previous stream operation was a kernel
   bool coarse_cluster = false;    // coarse levels of a V-cycle in one cluster kernel
-  int gs_pipeline = 1;            // streamed levels, pipelined sweep kernel: 0 never,
-                                  // 1 FP64 sweeps only (measured faster there), 2 always
+  int gs_pipeline = 1;            // pipelined sweep kernel: 0 never; on streamed levels
+                                  // 1 FP64 sweeps only (measured faster there), 2 always;
+                                  // 3 every level
   unsigned* pipe_err = nullptr;   // device word: a pipelined sweep's wait ran out
   int vc_cluster[2] = {0, 0};     // its cluster size per precision (0: not probed, <0: none)
 };

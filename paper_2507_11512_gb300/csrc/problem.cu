@@ -402,7 +402,6 @@ HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels, int pre_sweeps,
   if (rc == HPG_OK && !h->pipe_err) rc = dev_alloc((void**)&h->pipe_err, sizeof(unsigned) * 4);
   for (int l = 0; l < h->nlev && rc == HPG_OK; ++l) {
     Level& L = h->lev[l];
-    if (L.g.n_store * 27LL * 8 <= kStreamMatrixBytes) continue;
     long long maxrows = 0;
     for (int c = 0; c < kColours; ++c) maxrows = std::max(maxrows, L.g.off[c + 1] - L.g.off[c]);
     L.pipe_tiles = (int)((maxrows + kPipeTileRows - 1) / kPipeTileRows);
@@ -468,8 +467,8 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
     case HPG_OPT_COARSE_CLUSTER: h->coarse_cluster = value != 0; break;
     case HPG_OPT_PDL: h->pdl_enabled = value != 0; break;
     case HPG_OPT_GS_PIPELINE:
-      if (value < 0 || value > 2) {
-        set_error("hpg_set_option: HPG_OPT_GS_PIPELINE takes 0, 1 or 2, not %d", value);
+      if (value < 0 || value > 3) {
+        set_error("hpg_set_option: HPG_OPT_GS_PIPELINE takes 0..3, not %d", value);
         return HPG_ERR_INVALID;
       }
       h->gs_pipeline = value;

@@ -195,7 +195,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 // One row of a colour phase, arithmetic as gs_phase_kernel; gathers via L2.
-template <typename T, bool MASKED>
+template <typename T, bool STREAM, bool MASKED>
 __device__ __forceinline__ void pipe_row(const T* __restrict__ vals, const int* __restrict__ cols,
                                          long long ns, const T* __restrict__ r, T* z,
                                          long long row, long long valid_end, unsigned mask) {
@@ -208,23 +208,23 @@ __device__ __forceinline__ void pipe_row(const T* __restrict__ vals, const int* 
       T a = T(0);
       int c = 0;
       if (use) {
-        a = ld_matrix<true>(vals + s * ns + row);
-        c = ld_matrix<true>(cols + s * ns + row);
+        a = ld_matrix<STREAM>(vals + s * ns + row);
+        c = ld_matrix<STREAM>(cols + s * ns + row);
       }
       const T xv = (use && c < valid_end) ? __ldcg(z + c) : T(0);
       acc = fma(-a, xv, acc);
     } else {
-      const T a = ld_matrix<true>(vals + s * ns + row);
-      const int c = ld_matrix<true>(cols + s * ns + row);
+      const T a = ld_matrix<STREAM>(vals + s * ns + row);
+      const int c = ld_matrix<STREAM>(cols + s * ns + row);
       const T xv = (c < valid_end) ? __ldcg(z + c) : T(0);
       acc = fma(-a, xv, acc);
     }
   }
-  const T diag = ld_matrix<true>(vals + kCentre * ns + row);
+  const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
   z[row] = acc / diag;
 }
 
-template <typename T>
+template <typename T, bool STREAM>
 __global__ void __launch_bounds__(kPipeTileRows, 6)
 gs_pipeline_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                    const T* __restrict__ r, T* z, const __grid_constant__ PipePlan plan,
@@ -283,9 +283,9 @@ gs_pipeline_kernel(const T* __restrict__ vals, const int* __restrict__ cols, lon
     const long long lr = r0 + threadIdx.x;
     if (lr < ph.nrows) {
       if (ph.masked)
-        pipe_row<T, true>(vals, cols, ns, r, z, ph.row0 + lr, ph.valid_end, ph.mask);
+        pipe_row<T, STREAM, true>(vals, cols, ns, r, z, ph.row0 + lr, ph.valid_end, ph.mask);
       else
-        pipe_row<T, false>(vals, cols, ns, r, z, ph.row0 + lr, ph.valid_end, ph.mask);
+        pipe_row<T, STREAM, false>(vals, cols, ns, r, z, ph.row0 + lr, ph.valid_end, ph.mask);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -442,7 +442,7 @@ template <typename T>
 static int pipeline_grid(hpg_problem* h) {
   static int per_sm = 0;
   if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs_pipeline_kernel<T>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs_pipeline_kernel<T, true>,
                                                       kPipeTileRows, 0) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
@@ -491,9 +491,10 @@ static int symgs_pipelined(hpg_problem* h, int level, const T* r, T* z, bool fro
   return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32, bytes, s,
                 "gs_pipeline_kernel", [&] {
                   h->pdl_next = false;
-                  return kl(h, gs_pipeline_kernel<T>, grid, kPipeTileRows, s, Prec<T>::vals(L),
-                            L.cols, L.g.n_store, r, z, plan, L.pipe_flags, L.pipe_sync,
-                            h->pipe_err);
+                  const bool stream = L.g.n_store * 27LL * 8 > kStreamMatrixBytes;
+                  return kl(h, stream ? gs_pipeline_kernel<T, true> : gs_pipeline_kernel<T, false>,
+                            grid, kPipeTileRows, s, Prec<T>::vals(L), L.cols, L.g.n_store, r, z,
+                            plan, L.pipe_flags, L.pipe_sync, h->pipe_err);
                 });
 }
 
@@ -501,7 +502,10 @@ static int symgs_pipelined(hpg_problem* h, int level, const T* r, T* z, bool fro
 template <typename T>
 static int symgs(hpg_problem* h, int level, const T* r, T* z, bool from_zero, SweepState& st,
                  cudaStream_t s) {
-  const bool pipe = h->gs_pipeline == 2 || (h->gs_pipeline == 1 && sizeof(T) == 8);
+  const bool streamed_level = h->lev[level].g.n_store * 27LL * 8 > kStreamMatrixBytes;
+  const bool pipe = h->gs_pipeline == 3 ||
+                    (streamed_level && (h->gs_pipeline == 2 ||
+                                        (h->gs_pipeline == 1 && sizeof(T) == 8)));
   if (pipe && h->lev[level].pipe_flags && h->pipe_err)
     return symgs_pipelined<T>(h, level, r, z, from_zero, st, s);
   int rc;

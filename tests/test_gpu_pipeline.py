@@ -58,10 +58,10 @@ def test_pipelined_vcycle_equals_phase_launches(dtype):
     with hpg.Problem(80, 80, 80, beta=0.5) as p:
         r = storage_vec(p, dtype, 3)
         zs = []
-        for pipe in (0, 2):
+        for pipe in (0, 2, 3):
             hpg.set_option(p.h, GS_PIPELINE, pipe)
             zs.append(p.vcycle(r))
-        assert torch.equal(zs[0], zs[1])
+        assert torch.equal(zs[0], zs[1]) and torch.equal(zs[0], zs[2])
 
 
 @pytest.mark.parametrize("inner", [hpg.HPG_FP32, hpg.HPG_FP64])
@@ -72,14 +72,29 @@ def test_pipelined_solve_equals_phase_launches(inner):
         ones = torch.ones(n, dtype=torch.float64, device=DEV)
         b = p.to_natural(p.spmv(p.to_storage(ones)))
         res = []
-        for pipe in (0, 2, 2):
+        for pipe in (0, 2, 3):
             hpg.set_option(p.h, GS_PIPELINE, pipe)
             x = torch.zeros_like(b)
             info = hpg.gmres_ir_solve(p.h, b, x, tol=1e-9, inner=inner)
             assert info["status"] == 0 and info["converged"] == 1
             res.append((x, info["iterations"]))
         assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
-        assert torch.equal(res[1][0], res[2][0])
+        assert torch.equal(res[0][0], res[2][0]) and res[0][1] == res[2][1]
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16), (33, 17, 9), (2, 2, 2), (24, 20, 28)])
+def test_pipelined_sweeps_on_every_level_small_grids(dims):
+    with hpg.Problem(*dims, beta=0.5) as p:
+        for level in range(p.levels):
+            r = storage_vec(p, torch.float32, 5 + level, level)
+            zs = []
+            for pipe in (0, 3):
+                hpg.set_option(p.h, GS_PIPELINE, pipe)
+                zs.append(p.vcycle(r, level=level))
+                z = torch.zeros_like(r)
+                hpg.mg_smooth(p.h, level, r, z, 2, True)
+                zs.append(z)
+            assert torch.equal(zs[0], zs[2]) and torch.equal(zs[1], zs[3])
 
 
 def test_pipeline_option_values():
@@ -87,4 +102,4 @@ def test_pipeline_option_values():
         for v in (0, 1, 2):
             hpg.set_option(p.h, GS_PIPELINE, v)
         with pytest.raises(hpg.HpgError):
-            hpg.set_option(p.h, GS_PIPELINE, 3)
+            hpg.set_option(p.h, GS_PIPELINE, 4)
