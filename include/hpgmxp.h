@@ -372,6 +372,17 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
 #define HPG_OPT_GS_PIPELINE 3
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);
 
+/* Failure-detection test support (not a step of the method): the next
+ * pipelined sweep on `level` starts its tile queue at `tiles`, so the tiles
+ * below never run and the waits of the tiles after them on those run out
+ * (each wait is bounded, under a second); that sweep then abandons its
+ * remaining tiles and records the error, and the solve that contains it (or
+ * the next solve on this handle, for a sweep run through hpg_mg_smooth /
+ * hpg_mg_vcycle) returns HPG_ERR_TIMEOUT.  The device stays usable.  Only
+ * levels that have a pipelined sweep (HPG_OPT_GS_PIPELINE) are accepted.
+ * Synchronous. */
+HPG_API int hpg_inject_stall(hpg_problem_t* h, int level, int tiles);
+
 /* Frees everything the handle owns (NULL is accepted). */
 HPG_API int hpg_destroy(hpg_problem_t* h);
 

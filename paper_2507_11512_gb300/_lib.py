@@ -85,6 +85,7 @@ SIGNATURES = {
     "hpg_set_profiling": (_I, [_P, _I]),
     "hpg_set_execution": (_I, [_P, _I]),
     "hpg_set_option": (_I, [_P, _I, _I]),
+    "hpg_inject_stall": (_I, [_P, _I, _I]),
     "hpg_profile_report": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "hpg_destroy": (_I, [_P]),
     "hpg_status_string": (ctypes.c_char_p, [_I]),

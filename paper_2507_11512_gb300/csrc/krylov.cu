@@ -67,7 +67,6 @@ struct Workspace {
   double* t = nullptr;
   double* y = nullptr;
   double* rho2 = nullptr;  // ||r||^2 and max |r| of the outer residual
-  int* dev_err = nullptr;  // set by a kernel whose bounded wait gave up
   SolveState* st = nullptr;      // device
   SolveState* st_host = nullptr; // pinned mirror
   unsigned long long* hk = nullptr;  // [m] IF-node handles of the captured cycle
@@ -92,7 +91,7 @@ void destroy_workspace(hpg_problem* h) {
     if (ws->cap[i]) cudaStreamDestroy(ws->cap[i]);
   void* ptrs[] = {ws->Q,  ws->z,  ws->w,  ws->u,  ws->b,  ws->x,    ws->r,
                   ws->stage, ws->partials, ws->counter, ws->h1, ws->h2, ws->H, ws->cs,
-                  ws->sn, ws->t,  ws->y,  ws->rho2, ws->st, ws->hk, ws->dev_err,
+                  ws->sn, ws->t,  ws->y,  ws->rho2, ws->st, ws->hk,
                   ws->qscale, ws->qf};
   for (void* p : ptrs) dev_free(p);
   if (ws->st_host) cudaFreeHost(ws->st_host);
@@ -139,7 +138,6 @@ static int ensure_workspace(hpg_problem* h, int m, hpg_prec prec, hpg_prec basis
   rc = rc ? rc : dev_alloc((void**)&ws->y, 8 * (m + 1));
   rc = rc ? rc : dev_alloc((void**)&ws->st, sizeof(SolveState));
   rc = rc ? rc : dev_alloc((void**)&ws->rho2, 16);
-  rc = rc ? rc : dev_alloc((void**)&ws->dev_err, 16);
   rc = rc ? rc : dev_alloc((void**)&ws->hk, sizeof(unsigned long long) * (m + 1));
   for (int i = 0; i < 3 && rc == HPG_OK; ++i) {
     cudaError_t e = cudaStreamCreateWithFlags(&ws->cap[i], cudaStreamNonBlocking);
@@ -760,7 +758,6 @@ norm2_kernel(const double* __restrict__ v, long long ns, double* __restrict__ pa
 // ||r|| / ||b|| < tol ends the solve; so do a recorded breakdown / NaN and
 // maxit.  In graph mode it sets the WHILE node's condition.
 __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* st,
-                                   const int* __restrict__ dev_err,
                                    const unsigned* __restrict__ pipe_err, unsigned long long loop) {
   pdl_trigger();
   pdl_wait();
@@ -770,7 +767,7 @@ __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* 
   st->rho = rho;
   st->rel = rel;
   bool done = true;
-  if (*dev_err != 0 || (pipe_err && *pipe_err != 0)) {
+  if (pipe_err && *pipe_err != 0) {
     st->status = HPG_ERR_TIMEOUT;   // a kernel's bounded wait gave up
   } else if (!isfinite(rel)) {
     st->status = HPG_ERR_NAN;
@@ -981,7 +978,7 @@ static int enqueue_outer(hpg_problem* h, unsigned long long loop, cudaStream_t s
   if (rc) return rc;
   return launch(h, K_NORM, 0, HPG_FP64, 0.0, s, "outer_check_kernel", [&] {
     return kl(h, outer_check_kernel, 1, 32, s, (const double*)ws->rho2, ws->st,
-              (const int*)ws->dev_err, (const unsigned*)h->pipe_err, loop);
+              (const unsigned*)h->pipe_err, loop);
   });
 }
 
@@ -1234,7 +1231,6 @@ static int solve_t(hpg_problem* h, const double* b, double* x, double tol, int m
   h->pdl_next = false;
   const SolveState& fs = *ws->st_host;
   if (fs.status == HPG_ERR_TIMEOUT) {
-    HPG_CK(cudaMemset(ws->dev_err, 0, 16));
     if (h->pipe_err) HPG_CK(cudaMemset(h->pipe_err, 0, sizeof(unsigned) * 4));
     status = HPG_ERR_TIMEOUT;
     converged = false;

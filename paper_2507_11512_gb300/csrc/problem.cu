@@ -481,6 +481,16 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
   return HPG_OK;
 }
 
+HPG_API int hpg_inject_stall(hpg_problem_t* h, int level, int tiles) {
+  if (!h || level < 0 || level >= h->nlev || tiles < 0 || !h->lev[level].pipe_sync) {
+    set_error("hpg_inject_stall: invalid argument (level %d, tiles %d)", level, tiles);
+    return HPG_ERR_INVALID;
+  }
+  const unsigned v = (unsigned)tiles;
+  HPG_CK(cudaMemcpy(h->lev[level].pipe_sync + kPipeQueue, &v, sizeof(v), cudaMemcpyHostToDevice));
+  return HPG_OK;
+}
+
 HPG_API int hpg_destroy(hpg_problem_t* h) {
   if (!h) return HPG_OK;
   destroy_workspace(h);

@@ -103,3 +103,23 @@ def test_pipeline_option_values():
             hpg.set_option(p.h, GS_PIPELINE, v)
         with pytest.raises(hpg.HpgError):
             hpg.set_option(p.h, GS_PIPELINE, 4)
+
+
+def test_stalled_sweep_times_out_and_the_device_stays_usable():
+    """A tile whose predecessors never run: its bounded wait runs out, the
+    sweep records the error, the solve returns HPG_ERR_TIMEOUT, and the next
+    solve on the same handle is normal (no GPU fault: the waits end)."""
+    dims = (80, 80, 80)
+    n = 80 ** 3
+    with hpg.Problem(*dims, beta=0.5) as p:
+        ones = torch.ones(n, dtype=torch.float64, device=DEV)
+        b = p.to_natural(p.spmv(p.to_storage(ones)))
+        hpg.set_execution(p.h, hpg.HPG_EXEC_EAGER)   # the stall lands in the first V-cycle
+        assert hpg.load().hpg_inject_stall(p.h, 0, 1) == hpg.HPG_OK
+        x = torch.zeros_like(b)
+        info = hpg.gmres_ir_solve(p.h, b, x, tol=1e-9, inner=hpg.HPG_FP64, raise_on_error=False)
+        assert info["status"] == hpg.HPG_ERR_TIMEOUT and info["converged"] == 0
+        x.zero_()
+        info = hpg.gmres_ir_solve(p.h, b, x, tol=1e-9, inner=hpg.HPG_FP64)
+        assert info["status"] == 0 and info["converged"] == 1
+        assert hpg.load().hpg_inject_stall(p.h, 9, 1) == hpg.HPG_ERR_INVALID

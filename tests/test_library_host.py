@@ -72,6 +72,7 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.hpg_batch_solve(None, None, None, 1e-9, 10, None, None) == _lib.HPG_ERR_INVALID
     assert lib.hpg_batch_tune_solve(None, None, None, 1e-9, 10, None, None) == _lib.HPG_ERR_INVALID
     assert lib.hpg_batch_destroy(None) == _lib.HPG_OK
+    assert lib.hpg_inject_stall(None, 0, 1) == _lib.HPG_ERR_INVALID
     assert lib.hpg_build_mg_hierarchy(None, 4, 1, 1) == _lib.HPG_ERR_INVALID
     assert lib.hpg_destroy(None) == _lib.HPG_OK
     cnt = ctypes.c_int()
