@@ -287,17 +287,21 @@ def run_gpu(args):
     gflops = flops_sum / (ms_max / 1e3) / 1e9
     n_ir = infos[-1]["iterations"]
 
+    x_mxp = x.clone()   # the mixed-precision solution of the last timed solve
+
     # ---- FP64-only solve of the same code (Algorithm 2 as the paper's "double")
     fp64 = None
     if not args.no_fp64:
         ms64, infos64 = timed(hpg.HPG_FP64, max(1, args.steps // 2), 1)
+        err_vs_fp64 = (torch.linalg.norm(x_mxp - x) / torch.linalg.norm(x)).item()
         fl64 = sum(metrics.solve_flops(dims_list, metrics.cycles_from_info(
             i["iterations"], i["restarts"], w.restart)) for i in infos64)
         ms64_max, fl64_sum = reduce_max_sum([ms64, fl64], ["max", "sum"], dev)
         n_d = infos64[-1]["iterations"]
         fp64 = {"value": fl64_sum / (ms64_max / 1e3) / 1e9, "unit": "GFLOP/s",
                 "ms_per_solve": ms64_max / len(infos64), "iterations": n_d,
-                "rel_residual": infos64[-1]["rel_residual"]}
+                "rel_residual": infos64[-1]["rel_residual"],
+                "mxp_solution_rel_diff": err_vs_fp64}
 
     # ---- validation phase: n_d (FP64 GMRES) and n_ir (GMRES-IR) for the penalty
     valid = None
