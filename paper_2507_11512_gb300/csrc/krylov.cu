@@ -259,52 +259,60 @@ __host__ __device__ constexpr int pass_min_blocks() {
 // FP32 and FP64 elements move as float/double vector types (moving them
 // through integer vectors measured up to 2x slower for FP64 passes); 2-byte
 // elements move as packed integers.
-template <typename E, int V>
+// Load policy: KEEP leaves the lines in L2 (a later pass reads them again),
+// otherwise they stream (evict-first).
+template <bool KEEP, typename P>
+__device__ __forceinline__ P ld_policy(const P* p) {
+  if constexpr (KEEP) return __ldcg(p);
+  else return __ldcs(p);
+}
+
+template <typename E, int V, bool KEEP = false>
 __device__ __forceinline__ void ld_group(const E* p, E (&v)[V]) {
   if constexpr (sizeof(E) == 8 && V == 1) {
-    v[0] = __ldcs(p);
+    v[0] = ld_policy<KEEP>(p);
   } else if constexpr (sizeof(E) == 8) {
     static_assert(V % 2 == 0, "FP64 row groups of 1 or 2k elements");
 #pragma unroll
     for (int i = 0; i < V / 2; ++i) {
-      const double2 t = __ldcs(reinterpret_cast<const double2*>(p) + i);
+      const double2 t = ld_policy<KEEP>(reinterpret_cast<const double2*>(p) + i);
       v[2 * i] = t.x;
       v[2 * i + 1] = t.y;
     }
   } else if constexpr (sizeof(E) == 4 && V % 4 == 0) {
 #pragma unroll
     for (int i = 0; i < V / 4; ++i) {
-      const float4 t = __ldcs(reinterpret_cast<const float4*>(p) + i);
+      const float4 t = ld_policy<KEEP>(reinterpret_cast<const float4*>(p) + i);
       v[4 * i] = t.x;
       v[4 * i + 1] = t.y;
       v[4 * i + 2] = t.z;
       v[4 * i + 3] = t.w;
     }
   } else if constexpr (sizeof(E) == 4 && V == 2) {
-    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+    const float2 t = ld_policy<KEEP>(reinterpret_cast<const float2*>(p));
     v[0] = t.x;
     v[1] = t.y;
   } else if constexpr (sizeof(E) == 4) {
     static_assert(V == 1, "FP32 row groups of 1, 2 or 4k elements");
-    v[0] = __ldcs(p);
+    v[0] = ld_policy<KEEP>(p);
   } else {
     static_assert(sizeof(E) == 2, "2-, 4- or 8-byte elements");
     constexpr int bytes = 2 * V;
     if constexpr (bytes % 16 == 0) {
 #pragma unroll
       for (int i = 0; i < bytes / 16; ++i) {
-        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p) + i);
+        const uint4 t = ld_policy<KEEP>(reinterpret_cast<const uint4*>(p) + i);
         memcpy(reinterpret_cast<char*>(v) + 16 * i, &t, 16);
       }
     } else if constexpr (bytes == 8) {
-      const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
+      const uint2 t = ld_policy<KEEP>(reinterpret_cast<const uint2*>(p));
       memcpy(v, &t, 8);
     } else if constexpr (bytes == 4) {
-      const unsigned t = __ldcs(reinterpret_cast<const unsigned*>(p));
+      const unsigned t = ld_policy<KEEP>(reinterpret_cast<const unsigned*>(p));
       memcpy(v, &t, 4);
     } else {
       static_assert(bytes == 2, "2-byte row groups of 1, 2, 4 or 8k elements");
-      const unsigned short t = __ldcs(reinterpret_cast<const unsigned short*>(p));
+      const unsigned short t = ld_policy<KEEP>(reinterpret_cast<const unsigned short*>(p));
       memcpy(v, &t, 2);
     }
   }
@@ -511,15 +519,23 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
   T acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = T(0);
+  // Zig-zag over the passes: the reorth pass walks the rows backwards, so it
+  // starts on the rows the GEMVT pass read last (still in L2), and the final
+  // pass forwards again; the first two passes keep their lines in L2.
+  // (Measured at 128^3 GMRES(30): 0.8% faster solves than three forward,
+  // streaming passes.)
+  constexpr bool REV = KIND == kReorth;
+  constexpr bool KEEP = KIND != kFinal;
   const long long ng = ns / V;
   const long long stride = (long long)gridDim.x * kRedThreads;
   auto load = [&](long long g, T (&wr)[V], B (&q)[KMAX][V]) {
-    ld_group<T, V>(w + g * V, wr);
+    ld_group<T, V, KEEP>(w + g * V, wr);
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-      if (j < ncol) ld_group<B, V>(Q + j * ns + g * V, q[j]);
+      if (j < ncol) ld_group<B, V, KEEP>(Q + j * ns + g * V, q[j]);
   };
-  for (long long g = blockIdx.x * (long long)kRedThreads + threadIdx.x; g < ng; g += stride) {
+  for (long long gi = blockIdx.x * (long long)kRedThreads + threadIdx.x; gi < ng; gi += stride) {
+    const long long g = REV ? ng - 1 - gi : gi;
     T wr[V];
     B q[KMAX][V];
     load(g, wr, q);
