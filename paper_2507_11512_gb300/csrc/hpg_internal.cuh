@@ -114,7 +114,7 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
 // neighbour colour is below c: colours not yet visited are still zero, so
 // their entries need not even be loaded.  An odd offset along an axis flips
 // that axis's parity bit of the colour.
-__host__ __device__ inline unsigned gs_slot_mask(int c, bool from_zero) {
+__host__ __device__ constexpr unsigned gs_slot_mask(int c, bool from_zero) {
   if (!from_zero) return (1u << 27) - 1u;
   unsigned m = 1u << 13;
   for (int s = 0; s < 27; ++s) {

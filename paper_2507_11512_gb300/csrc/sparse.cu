@@ -81,11 +81,19 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
 // matrix read evict-first.  Launched without programmatic overlap: measured on
 // GB300, letting the next phase's CTAs start early (or prefetching its slots
 // into L2) slows this bandwidth-bound chain down.
-template <typename T, bool STREAM, bool MASKED>
+//
+// MC = -1 reads every slot.  MC = c (0..7) is the phase of colour c in the
+// first forward sweep from z = 0: only the slots whose neighbour colour is
+// below c are loaded (the others multiply zeros), and the set is fixed at
+// compile time, so the loads of a row issue as one straight-line batch.  A
+// run-time slot mask made these phases no faster than full ones on GB300
+// (colour 0, which loads only the diagonal, took 70 % of a full phase).
+template <typename T, bool STREAM, int MC>
 __global__ void __launch_bounds__(256, 8)
 gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                 const T* __restrict__ r, T* x, long long row0, long long nrows,
-                long long valid_end, unsigned mask) {
+                long long valid_end) {
+  constexpr unsigned kMask = MC < 0 ? (1u << kSlots) - 1u : gs_slot_mask(MC, true);
   pdl_wait();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nrows) return;
@@ -93,27 +101,33 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
   T acc = r[row];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
-    if (s == kCentre) continue;
-    if (MASKED) {
-      // slots outside `mask` are known zero: predicated off, not loaded
-      const bool use = (mask >> s) & 1u;
-      T a = T(0);
-      int c = 0;
-      if (use) {
-        a = ld_matrix<STREAM>(vals + s * ns + row);
-        c = ld_matrix<STREAM>(cols + s * ns + row);
-      }
-      const T xv = (use && c < valid_end) ? __ldg(x + c) : T(0);
-      acc = fma(-a, xv, acc);
-    } else {
-      const T a = ld_matrix<STREAM>(vals + s * ns + row);
-      const int c = ld_matrix<STREAM>(cols + s * ns + row);
-      const T xv = (c < valid_end) ? __ldg(x + c) : T(0);
-      acc = fma(-a, xv, acc);
-    }
+    if (s == kCentre || !((kMask >> s) & 1u)) continue;
+    const T a = ld_matrix<STREAM>(vals + s * ns + row);
+    const int c = ld_matrix<STREAM>(cols + s * ns + row);
+    const T xv = (c < valid_end) ? __ldg(x + c) : T(0);
+    acc = fma(-a, xv, acc);
   }
   const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
   x[row] = acc / diag;
+}
+
+// The bandwidth-variant instantiation of a phase of colour c.
+template <typename T, bool STREAM>
+using GsPhaseFn = void (*)(const T*, const int*, long long, const T*, T*, long long, long long,
+                           long long);
+template <typename T, bool STREAM>
+static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
+  if (!from_zero) return gs_phase_kernel<T, STREAM, -1>;
+  switch (c) {
+    case 0: return gs_phase_kernel<T, STREAM, 0>;
+    case 1: return gs_phase_kernel<T, STREAM, 1>;
+    case 2: return gs_phase_kernel<T, STREAM, 2>;
+    case 3: return gs_phase_kernel<T, STREAM, 3>;
+    case 4: return gs_phase_kernel<T, STREAM, 4>;
+    case 5: return gs_phase_kernel<T, STREAM, 5>;
+    case 6: return gs_phase_kernel<T, STREAM, 6>;
+    default: return gs_phase_kernel<T, STREAM, 7>;
+  }
 }
 
 // Latency variant, for coarse levels (matrix resident in L2, at most a few
@@ -424,16 +438,13 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                 "gs_phase_kernel", [&] {
                   if (L.g.n_store * 27LL * 8 > kStreamMatrixBytes) {
                     h->pdl_next = false;   // full serialisation (see gs_phase_kernel)
-                    if (keep)   // slice read again two phases later: leave it in L2
-                      return kl(h, from_zero ? gs_phase_kernel<T, false, true>
-                                             : gs_phase_kernel<T, false, false>,
+                    if (keep)   // slice read again soon after: leave it in L2
+                      return kl(h, gs_phase_fn<T, false>(c, from_zero),
                                 grid_for(nrows, kThreads), kThreads, s, vals, L.cols,
-                                L.g.n_store, r, z, row0, nrows, valid_end,
-                                gs_slot_mask(c, from_zero));
-                    return kl(h, from_zero ? gs_phase_kernel<T, true, true>
-                                           : gs_phase_kernel<T, true, false>,
-                              grid_for(nrows, kThreads), kThreads, s, vals, L.cols, L.g.n_store,
-                              r, z, row0, nrows, valid_end, gs_slot_mask(c, from_zero));
+                                L.g.n_store, r, z, row0, nrows, valid_end);
+                    return kl(h, gs_phase_fn<T, true>(c, from_zero), grid_for(nrows, kThreads),
+                              kThreads, s, vals, L.cols, L.g.n_store, r, z, row0, nrows,
+                              valid_end);
                   }
                   // measured on GB300: programmatic overlap helps the smallest
                   // phases and slows phases of tens of thousands of rows
@@ -521,8 +532,11 @@ static int symgs(hpg_problem* h, int level, const T* r, T* z, bool from_zero, Sw
   // measured 1.2 % faster solves at 128^3 FP32
   for (int c = 0; c < kColours; ++c)
     if ((rc = gs_phase<T>(h, level, r, z, c, from_zero, st, s, c == kColours - 2))) return rc;
+  // the last phase (colour 0) leaves its slice in L2 too: after the
+  // post-smoothing, the Krylov SpMV reads the matrix from the colour-0 block
+  // on; measured 0.3 % faster solves
   for (int c = kColours - 1; c >= 0; --c)
-    if ((rc = gs_phase<T>(h, level, r, z, c, false, st, s))) return rc;
+    if ((rc = gs_phase<T>(h, level, r, z, c, false, st, s, c == 0))) return rc;
   return HPG_OK;
 }
 
