@@ -85,9 +85,50 @@ __device__ __forceinline__ V ld_matrix(const V* p) {
   return __ldg(p);
 }
 
+// Load marked evict-last in L2 (an L2 cache policy made by createpolicy).
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float ld_evict_last(const float* p) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;"
+      : "=f"(v) : "l"(p), "l"(l2_evict_last_policy()));
+  return v;
+}
+__device__ __forceinline__ double ld_evict_last(const double* p) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;"
+      : "=d"(v) : "l"(p), "l"(l2_evict_last_policy()));
+  return v;
+}
+__device__ __forceinline__ int ld_evict_last(const int* p) {
+  int v;
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;"
+      : "=r"(v) : "l"(p), "l"(l2_evict_last_policy()));
+  return v;
+}
+
+// How a kernel reads a level's matrix: streamed evict-first (levels larger
+// than L2), cached normally, or marked evict-last (the small coarse levels,
+// read by every V-cycle: without the mark the finest level's traffic pushes
+// them out of L2 between V-cycles).
+enum MatLoad { kMatStream = 0, kMatCached = 1, kMatResident = 2 };
+template <int MODE, typename V>
+__device__ __forceinline__ V ld_mat(const V* p) {
+  if constexpr (MODE == kMatStream) return __ldcs(p);
+  else if constexpr (MODE == kMatResident) return ld_evict_last(p);
+  else return __ldg(p);
+}
+
 // Levels whose FP32 ELL slots exceed this many bytes stream their matrix
 // (evict-first); smaller (coarse) levels keep theirs in the 126 MB L2.
 constexpr long long kStreamMatrixBytes = 96LL << 20;
+// Levels whose FP32 ELL slots take at most this many bytes are read
+// evict-last.  Measured on GB300 at 128^3: marking the 57 MB level 1 as well
+// made its sweeps 2.5x slower, even alone.
+constexpr long long kResidentMatrixBytes = 16LL << 20;
 
 // ---------------------------------------------- programmatic dependent launch
 // Kernels of the solve chain are launched with programmatic stream

@@ -2,10 +2,13 @@
 // phase of multicolour Gauss-Seidel, the fused residual-restriction and the
 // injection prolongation, plus the V-cycle that strings them together.
 //
-// All kernels read the slot-major ELL arrays with streaming (evict-first)
-// loads and gather x through the read-only path; rows of one colour block are
-// contiguous, so a warp reads each slot of 32 consecutive rows as one 128-byte
-// (FP32) or 256-byte (FP64) transaction.
+// Kernels read the slot-major ELL arrays by level size: streaming
+// (evict-first) where the matrix is larger than L2, normally cached on
+// mid-size levels, and marked evict-last on the small coarse levels (read by
+// every V-cycle; measured on GB300 at 128^3, this cut a V-cycle from 570 to
+// 494 us).  x is gathered through the read-only path; rows of one colour block
+// are contiguous, so a warp reads each slot of 32 consecutive rows as one
+// 128-byte (FP32) or 256-byte (FP64) transaction.
 
 #include <string.h>
 
@@ -136,7 +139,7 @@ static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
 // programmatic wait -- the matrix does not depend on earlier kernels -- so that
 // latency overlaps the previous phase; after the wait it issues all the
 // gathers of x at once.  Same slot order and arithmetic as gs_phase_kernel.
-template <typename T>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(64)
 gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                       const T* __restrict__ r, T* x, long long row0, long long nrows,
@@ -149,8 +152,8 @@ gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, 
   T a[kSlots];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
-    col[s] = live ? __ldg(cols + s * ns + row) : 0;
-    a[s] = live ? __ldg(vals + s * ns + row) : T(1);
+    col[s] = live ? ld_mat<MODE>(cols + s * ns + row) : 0;
+    a[s] = live ? ld_mat<MODE>(vals + s * ns + row) : T(1);
   }
   pdl_wait();
   if (!live) return;
@@ -325,7 +328,7 @@ gs_pipeline_kernel(const T* __restrict__ vals, const int* __restrict__ cols, lon
 // coarse-coincident fine points are exactly fine colour block 7, stored in the
 // same lexicographic order as the coarse grid, so threads walk that block
 // contiguously and scatter into the coarse colour blocks.
-template <typename T, bool STREAM>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
 restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                 const T* __restrict__ vals, const int* __restrict__ cols,
@@ -342,8 +345,8 @@ restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc
   T acc = r[row];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
-    const T a = ld_matrix<STREAM>(vals + s * ns + row);
-    const int c = ld_matrix<STREAM>(cols + s * ns + row);
+    const T a = ld_mat<MODE>(vals + s * ns + row);
+    const int c = ld_mat<MODE>(cols + s * ns + row);
     acc = fma(-a, __ldg(z + c), acc);
   }
   const int I = (int)(p % cx);
@@ -374,6 +377,22 @@ prolong_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
 // ----------------------------------------------------------------- launchers
 constexpr int kThreads = 256;
 constexpr long long kPdlSmallRows = 16384;   // latency-variant phases overlapped up to this
+
+// MatLoad of a level (by its FP32 ELL slot bytes).
+static int mat_mode(const Level& L) {
+  const long long b = L.g.n_store * 27LL * 8;
+  return b > kStreamMatrixBytes ? kMatStream : b > kResidentMatrixBytes ? kMatCached
+                                                                        : kMatResident;
+}
+
+template <typename T>
+static auto restrict_fn(const Level& L) -> decltype(&restrict_kernel<T, kMatStream>) {
+  switch (mat_mode(L)) {
+    case kMatStream: return restrict_kernel<T, kMatStream>;
+    case kMatCached: return restrict_kernel<T, kMatCached>;
+    default: return restrict_kernel<T, kMatResident>;
+  }
+}
 
 // Algorithmic DRAM bytes per row (ELL with 27 padded slots, int32 indices;
 // every vector entry read or written once).  sv / sx: value / vector bytes.
@@ -449,8 +468,11 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                   // measured on GB300: programmatic overlap helps the smallest
                   // phases and slows phases of tens of thousands of rows
                   if (nrows > kPdlSmallRows) h->pdl_next = false;
-                  return kl(h, gs_phase_small_kernel<T>, grid_for(nrows, 64), 64, s, vals,
-                            L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                  return kl(h,
+                            mat_mode(L) == kMatResident ? gs_phase_small_kernel<T, kMatResident>
+                                                        : gs_phase_small_kernel<T, kMatCached>,
+                            grid_for(nrows, 64), 64, s, vals, L.cols, L.g.n_store, r, z, row0,
+                            nrows, valid_end);
                 });
 }
 
@@ -562,10 +584,8 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   const T* vals = Prec<T>::vals(L);
   rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
               "restrict_kernel", [&] {
-                const bool stream = L.g.n_store * 27LL * 8 > kStreamMatrixBytes;
-                return kl(h, stream ? restrict_kernel<T, true> : restrict_kernel<T, false>,
-                          grid_for(cnt, kThreads), kThreads, s, L.g, C.g, vals, L.cols, r, z,
-                          rc_vec);
+                return kl(h, restrict_fn<T>(L), grid_for(cnt, kThreads), kThreads, s, L.g,
+                          C.g, vals, L.cols, r, z, rc_vec);
               });
   if (rc) return rc;
   if ((rc = vcycle_t<T>(h, l + 1, rc_vec, zc_vec, s))) return rc;
@@ -724,10 +744,8 @@ static int vcycle_noalloc_t(hpg_problem* h, int l, const T* r, T* z, T* const* c
   const T* vals = Prec<T>::vals(L);
   rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
               "restrict_kernel", [&] {
-                const bool stream = L.g.n_store * 27LL * 8 > kStreamMatrixBytes;
-                return kl(h, stream ? restrict_kernel<T, true> : restrict_kernel<T, false>,
-                          grid_for(cnt, kThreads), kThreads, s, L.g, C.g, vals, L.cols, r, z,
-                          rc_vec);
+                return kl(h, restrict_fn<T>(L), grid_for(cnt, kThreads), kThreads, s, L.g,
+                          C.g, vals, L.cols, r, z, rc_vec);
               });
   if (rc) return rc;
   if ((rc = vcycle_noalloc_t<T>(h, l + 1, rc_vec, zc_vec, crhs, csol, s))) return rc;
