@@ -502,7 +502,8 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
                  const double* __restrict__ h2, T* wout, double* __restrict__ partials,
                  unsigned int* counter, double* __restrict__ out, double* __restrict__ H,
                  int ldh, double* __restrict__ cs, double* __restrict__ sn,
-                 double* __restrict__ t, SolveState* st, unsigned long long next) {
+                 double* __restrict__ t, SolveState* st, unsigned long long next,
+                 int zigzag) {
   constexpr int V = pass_vec<B, KMAX>();
   constexpr bool S = basis_scaled<B>();
   constexpr bool MAXLAST = S && KIND == kFinal;
@@ -519,23 +520,31 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
   T acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = T(0);
-  // Zig-zag over the passes: the reorth pass walks the rows backwards, so it
-  // starts on the rows the GEMVT pass read last (still in L2), and the final
-  // pass forwards again; the first two passes keep their lines in L2.
-  // (Measured at 128^3 GMRES(30): 0.8% faster solves than three forward,
-  // streaming passes.)
-  constexpr bool REV = KIND == kReorth;
-  constexpr bool KEEP = KIND != kFinal;
+  // Zig-zag over the passes (zigzag != 0, basis vectors much smaller than
+  // L2): the reorth pass walks the rows backwards, so it starts on the rows
+  // the GEMVT pass read last (still in L2), and the final pass forwards again;
+  // the first two passes keep their lines in L2.  Measured on GB300: 0.8 %
+  // faster 128^3 GMRES(30) solves; with 131 MB vectors (320^3) the backward
+  // pass streamed at half the rate of a forward one.
+  const bool rev = zigzag && KIND == kReorth;
+  const bool keep = zigzag && KIND != kFinal;
   const long long ng = ns / V;
   const long long stride = (long long)gridDim.x * kRedThreads;
   auto load = [&](long long g, T (&wr)[V], B (&q)[KMAX][V]) {
-    ld_group<T, V, KEEP>(w + g * V, wr);
+    if (keep) {
+      ld_group<T, V, true>(w + g * V, wr);
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j < ncol) ld_group<B, V, KEEP>(Q + j * ns + g * V, q[j]);
+      for (int j = 0; j < KMAX; ++j)
+        if (j < ncol) ld_group<B, V, true>(Q + j * ns + g * V, q[j]);
+    } else {
+      ld_group<T, V, false>(w + g * V, wr);
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j)
+        if (j < ncol) ld_group<B, V, false>(Q + j * ns + g * V, q[j]);
+    }
   };
   for (long long gi = blockIdx.x * (long long)kRedThreads + threadIdx.x; gi < ng; gi += stride) {
-    const long long g = REV ? ng - 1 - gi : gi;
+    const long long g = rev ? ng - 1 - gi : gi;
     T wr[V];
     B q[KMAX][V];
     load(g, wr, q);
@@ -862,6 +871,9 @@ __global__ void delay_kernel(long long cycles) {
 // ----------------------------------------------------------------- launchers
 template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? HPG_FP64 : HPG_FP32; }
 
+// Basis vectors up to this size take the zig-zag pass order (cgs2_pass_kernel).
+constexpr long long kZigZagVectorBytes = 32LL << 20;
+
 // Grid of a CGS2 pass: every resident block of the instantiation (one wave
 // of grid-stride blocks), at most the G blocks the partials are sized for.
 template <typename T, typename B, int KMAX, int KIND>
@@ -887,7 +899,8 @@ static cudaError_t enqueue_pass(hpg_problem* h, const B* Q, long long ns, int nc
   return kl(h, cgs2_pass_kernel<T, B, KMAX, KIND>, pass_grid<T, B, KMAX, KIND>(h), kRedThreads,
             s, Q, ns, ncol, w, (const float*)ws->qscale, (const double*)ws->h1,
             (const double*)ws->h2, wout, ws->partials, ws->counter, out, ws->H, ws->m + 1,
-            ws->cs, ws->sn, ws->t, ws->st, next);
+            ws->cs, ws->sn, ws->t, ws->st, next,
+            ns * (long long)sizeof(B) <= kZigZagVectorBytes ? 1 : 0);
 }
 
 // One CGS2 pass over q_0..q_{ncol-1} (k = ncol - 1); the final pass also

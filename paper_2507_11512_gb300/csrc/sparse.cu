@@ -378,6 +378,10 @@ prolong_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
 constexpr int kThreads = 256;
 constexpr long long kPdlSmallRows = 16384;   // latency-variant phases overlapped up to this
 
+// Largest colour slice (values + indices) a streamed level's phase leaves in
+// L2 for a later phase (symgs).
+constexpr long long kKeepSliceBytes = 96LL << 20;
+
 // MatLoad of a level (by its FP32 ELL slot bytes).
 static int mat_mode(const Level& L) {
   const long long b = L.g.n_store * 27LL * 8;
@@ -549,16 +553,22 @@ static int symgs(hpg_problem* h, int level, const T* r, T* z, bool from_zero, Sw
   if (pipe && h->lev[level].pipe_flags && h->pipe_err)
     return symgs_pipelined<T>(h, level, r, z, from_zero, st, s);
   int rc;
+  // Where a colour's slice of the matrix fits in L2 with room to spare:
   // the slice of colour kColours - 2 is read again right after the turning
-  // colour: its forward phase leaves it in L2 (the others stream evict-first);
-  // measured 1.2 % faster solves at 128^3 FP32
+  // colour, so its forward phase leaves it in L2 (the others stream
+  // evict-first); measured 1.2 % faster solves at 128^3 FP32.  The last phase
+  // (colour 0) leaves its slice in L2 too: after the post-smoothing, the
+  // Krylov SpMV reads the matrix from the colour-0 block on; 0.3 % faster.
+  const Level& L = h->lev[level];
+  const auto fits = [&](int c) {
+    return (double)(L.g.off[c + 1] - L.g.off[c]) * kSlots * (sizeof(T) + 4.0) <=
+           (double)kKeepSliceBytes;
+  };
   for (int c = 0; c < kColours; ++c)
-    if ((rc = gs_phase<T>(h, level, r, z, c, from_zero, st, s, c == kColours - 2))) return rc;
-  // the last phase (colour 0) leaves its slice in L2 too: after the
-  // post-smoothing, the Krylov SpMV reads the matrix from the colour-0 block
-  // on; measured 0.3 % faster solves
+    if ((rc = gs_phase<T>(h, level, r, z, c, from_zero, st, s, c == kColours - 2 && fits(c))))
+      return rc;
   for (int c = kColours - 1; c >= 0; --c)
-    if ((rc = gs_phase<T>(h, level, r, z, c, false, st, s, c == 0))) return rc;
+    if ((rc = gs_phase<T>(h, level, r, z, c, false, st, s, c == 0 && fits(c)))) return rc;
   return HPG_OK;
 }
 
