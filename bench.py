@@ -33,18 +33,33 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes (read + write) per launch of the level-0 FP32 Gauss-Seidel phase
 # kernel at 128^3, from one ncu capture (profiles/gs_phase_level0_128cube.md),
-# valid while the kernel sources hash to `sources_sha256`.
-GS_TRAFFIC = {"workload": "mxp_gmres30_128cube", "bytes_per_launch": 65346048.0,
-              "sources_sha256": "54d71c2ac4eb47e887c92c558329833224c2f8152e9840df9cb2a445b64a9798"}
-GS_SOURCES = ("paper_2507_11512_gb300/csrc/sparse.cu", "paper_2507_11512_gb300/csrc/hpg_internal.cuh")
+# valid while the kernel's source text (the kernel and the helpers it
+# inlines) hashes to `sources_sha256`.
+GS_TRAFFIC = {"workload": "mxp_gmres30_128cube", "bytes_per_launch": 65260544.0,
+              "sources_sha256": "be7a8b35e8d1a3a25d975a4e6077c2f46a04750886dc46d82ca8dfe415cc897b"}
+# (file, first line of the block, text that ends it): the kernel's source
+GS_KERNEL_TEXT = (
+    ("paper_2507_11512_gb300/csrc/sparse.cu", "template <typename T, bool STREAM, int MC>",
+     "// The bandwidth-variant instantiation"),
+    ("paper_2507_11512_gb300/csrc/hpg_internal.cuh", "template <bool STREAM, typename V>", "\n}\n"),
+    ("paper_2507_11512_gb300/csrc/hpg_internal.cuh",
+     "__host__ __device__ constexpr unsigned gs_slot_mask", "\n}\n"),
+)
 
 
 def gs_sources_sha256():
+    """sha256 of the Gauss-Seidel phase kernel's source blocks (None if a
+    block is not found)."""
     import hashlib
     h = hashlib.sha256()
-    for rel in GS_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+    for rel, start, end in GS_KERNEL_TEXT:
+        with open(os.path.join(ROOT, rel)) as f:
+            text = f.read()
+        i = text.find(start)
+        j = text.find(end, i + len(start)) if i >= 0 else -1
+        if i < 0 or j < 0:
+            return None
+        h.update(text[i:j + len(end)].encode())
     return h.hexdigest()
 
 
@@ -53,8 +68,8 @@ def gs_traffic(workload="mxp_gmres30_128cube"):
     (or the capture was of another workload)."""
     if GS_TRAFFIC["bytes_per_launch"] is None or workload != GS_TRAFFIC["workload"]:
         return None
-    return GS_TRAFFIC["bytes_per_launch"] if gs_sources_sha256() == GS_TRAFFIC[
-        "sources_sha256"] else None
+    sha = gs_sources_sha256()
+    return GS_TRAFFIC["bytes_per_launch"] if sha and sha == GS_TRAFFIC["sources_sha256"] else None
 
 
 def parse():
