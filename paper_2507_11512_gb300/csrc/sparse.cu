@@ -139,6 +139,8 @@ static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
 // programmatic wait -- the matrix does not depend on earlier kernels -- so that
 // latency overlaps the previous phase; after the wait it issues all the
 // gathers of x at once.  Same slot order and arithmetic as gs_phase_kernel.
+// MODE (MatLoad): kMatCached, or kMatResident for the small levels whose
+// matrix is kept in L2 evict-last.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(64)
 gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
@@ -470,7 +472,9 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                               valid_end);
                   }
                   // measured on GB300: programmatic overlap helps the smallest
-                  // phases and slows phases of tens of thousands of rows
+                  // phases and slows phases of tens of thousands of rows (with
+                  // the 32768-row level-1 phases overlapped too, the 128^3
+                  // solve took 110.3 ms instead of 107.4)
                   if (nrows > kPdlSmallRows) h->pdl_next = false;
                   return kl(h,
                             mat_mode(L) == kMatResident ? gs_phase_small_kernel<T, kMatResident>
