@@ -140,12 +140,15 @@ static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
 // latency overlaps the previous phase; after the wait it issues all the
 // gathers of x at once.  Same slot order and arithmetic as gs_phase_kernel.
 // MODE (MatLoad): kMatCached, or kMatResident for the small levels whose
-// matrix is kept in L2 evict-last.
-template <typename T, int MODE>
+// matrix is kept in L2 evict-last.  MC as in gs_phase_kernel: -1 all slots,
+// c the first forward sweep's colour c (slots with a later neighbour colour
+// are neither loaded nor gathered).
+template <typename T, int MODE, int MC>
 __global__ void __launch_bounds__(64)
 gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                       const T* __restrict__ r, T* x, long long row0, long long nrows,
                       long long valid_end) {
+  constexpr unsigned kMask = MC < 0 ? (1u << kSlots) - 1u : gs_slot_mask(MC, true);
   pdl_trigger();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool live = t < nrows;
@@ -154,20 +157,46 @@ gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, 
   T a[kSlots];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
-    col[s] = live ? ld_mat<MODE>(cols + s * ns + row) : 0;
-    a[s] = live ? ld_mat<MODE>(vals + s * ns + row) : T(1);
+    const bool use = live && ((kMask >> s) & 1u);
+    col[s] = use ? ld_mat<MODE>(cols + s * ns + row) : 0;
+    a[s] = use ? ld_mat<MODE>(vals + s * ns + row) : T(1);
   }
   pdl_wait();
   if (!live) return;
   T xv[kSlots];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s)
-    xv[s] = (s != kCentre && col[s] < valid_end) ? __ldg(x + col[s]) : T(0);
+    xv[s] = (s != kCentre && ((kMask >> s) & 1u) && col[s] < valid_end) ? __ldg(x + col[s])
+                                                                        : T(0);
   T acc = r[row];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s)
-    if (s != kCentre) acc = fma(-a[s], xv[s], acc);
+    if (s != kCentre && ((kMask >> s) & 1u)) acc = fma(-a[s], xv[s], acc);
   x[row] = acc / a[kCentre];
+}
+
+// The latency-variant instantiation of a phase of colour c.
+template <typename T>
+using GsSmallFn = void (*)(const T*, const int*, long long, const T*, T*, long long, long long,
+                           long long);
+template <typename T, int MODE>
+static GsSmallFn<T> gs_small_fn_mode(int c, bool from_zero) {
+  if (!from_zero) return gs_phase_small_kernel<T, MODE, -1>;
+  switch (c) {
+    case 0: return gs_phase_small_kernel<T, MODE, 0>;
+    case 1: return gs_phase_small_kernel<T, MODE, 1>;
+    case 2: return gs_phase_small_kernel<T, MODE, 2>;
+    case 3: return gs_phase_small_kernel<T, MODE, 3>;
+    case 4: return gs_phase_small_kernel<T, MODE, 4>;
+    case 5: return gs_phase_small_kernel<T, MODE, 5>;
+    case 6: return gs_phase_small_kernel<T, MODE, 6>;
+    default: return gs_phase_small_kernel<T, MODE, 7>;
+  }
+}
+template <typename T>
+static GsSmallFn<T> gs_small_fn(int mode, int c, bool from_zero) {
+  return mode == kMatResident ? gs_small_fn_mode<T, kMatResident>(c, from_zero)
+                              : gs_small_fn_mode<T, kMatCached>(c, from_zero);
 }
 
 // ---------------------------------------------- pipelined symmetric sweep
@@ -476,11 +505,8 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                   // the 32768-row level-1 phases overlapped too, the 128^3
                   // solve took 110.3 ms instead of 107.4)
                   if (nrows > kPdlSmallRows) h->pdl_next = false;
-                  return kl(h,
-                            mat_mode(L) == kMatResident ? gs_phase_small_kernel<T, kMatResident>
-                                                        : gs_phase_small_kernel<T, kMatCached>,
-                            grid_for(nrows, 64), 64, s, vals, L.cols, L.g.n_store, r, z, row0,
-                            nrows, valid_end);
+                  return kl(h, gs_small_fn<T>(mat_mode(L), c, from_zero), grid_for(nrows, 64),
+                            64, s, vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
                 });
 }
 
