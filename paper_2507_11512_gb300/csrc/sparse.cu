@@ -359,11 +359,17 @@ gs_pipeline_kernel(const T* __restrict__ vals, const int* __restrict__ cols, lon
 // coarse-coincident fine points are exactly fine colour block 7, stored in the
 // same lexicographic order as the coarse grid, so threads walk that block
 // contiguously and scatter into the coarse colour blocks.
+//
+// zc0 (optional): the coarse level's first forward sweep from zero starts
+// with colour 0, whose rows have no neighbour of a lower colour, so that
+// phase is z_I = rc_I / a_II; with zc0 set it is done here, for the coarse
+// points of colour 0, and the sweep skips the phase (same values).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
 restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                 const T* __restrict__ vals, const int* __restrict__ cols,
-                const T* __restrict__ r, const T* __restrict__ z, T* __restrict__ rc) {
+                const T* __restrict__ r, const T* __restrict__ z, T* __restrict__ rc,
+                T* __restrict__ zc0, const T* __restrict__ cdiag) {
   pdl_trigger();
   const int cx = gf.cdx[kCoarseColour], cy = gf.cdy[kCoarseColour];
   const long long cnt = (long long)cx * cy * gf.cdz[kCoarseColour];
@@ -383,7 +389,9 @@ restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc
   const int I = (int)(p % cx);
   const int J = (int)((p / cx) % cy);
   const int K = (int)(p / ((long long)cx * cy));
-  rc[store_index(gc, I, J, K)] = acc;
+  const long long R = store_index(gc, I, J, K);
+  rc[R] = acc;
+  if (zc0 && colour_of(I, J, K) == 0) zc0[R] = acc / cdiag[R];
 }
 
 // Prolongation P = R^T and correction (Fig. 1, eq. (3) transposed):
@@ -602,10 +610,20 @@ static int symgs(hpg_problem* h, int level, const T* r, T* z, bool from_zero, Sw
   return HPG_OK;
 }
 
+// Whether the restriction from level l also runs the first phase (colour 0)
+// of level l+1's first sweep from zero: true when that sweep goes through the
+// launched phases (not the cluster kernel) and starts from zero (the
+// coarsest level, or a pre-smoother).
+static bool fuse_first_phase(const hpg_problem* h, int l) {
+  return !h->coarse_cluster && (l + 1 == h->nlev - 1 || h->pre >= 1);
+}
+
 template <typename T>
-static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
+static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s,
+                    bool c0_done = false) {
   const Level& L = h->lev[l];
   SweepState st;
+  if (c0_done) st.last = 0;   // colour 0 of the first sweep came with the restriction
   int rc = launch_vcycle_cluster(h, l, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32, r, z, s);
   if (rc != HPG_ERR_UNSUPPORTED) return rc;   // small level: the rest runs in one cluster
   if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
@@ -618,6 +636,7 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   const Level& C = h->lev[l + 1];
   T* rc_vec = (T*)C.rhs[Prec<T>::idx];
   T* zc_vec = (T*)C.sol[Prec<T>::idx];
+  const bool fuse = fuse_first_phase(h, l);
   const long long cnt = (long long)L.g.cdx[kCoarseColour] * L.g.cdy[kCoarseColour] *
                         L.g.cdz[kCoarseColour];
   const int prec = Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32;
@@ -625,10 +644,11 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s) {
   rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
               "restrict_kernel", [&] {
                 return kl(h, restrict_fn<T>(L), grid_for(cnt, kThreads), kThreads, s, L.g,
-                          C.g, vals, L.cols, r, z, rc_vec);
+                          C.g, vals, L.cols, r, z, rc_vec, fuse ? zc_vec : (T*)nullptr,
+                          Prec<T>::vals(C) + kCentre * C.g.n_store);
               });
   if (rc) return rc;
-  if ((rc = vcycle_t<T>(h, l + 1, rc_vec, zc_vec, s))) return rc;
+  if ((rc = vcycle_t<T>(h, l + 1, rc_vec, zc_vec, s, fuse))) return rc;
   rc = launch(h, K_PROLONG, l, prec, cnt * 3.0 * sizeof(T), s, "prolong_kernel", [&] {
     return kl(h, prolong_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
               (const T*)zc_vec, z);
@@ -764,9 +784,10 @@ static int scratch_address(void** out) {
 // Same schedule as vcycle_t; coarse vectors come from crhs / csol.
 template <typename T>
 static int vcycle_noalloc_t(hpg_problem* h, int l, const T* r, T* z, T* const* crhs,
-                            T* const* csol, cudaStream_t s) {
+                            T* const* csol, cudaStream_t s, bool c0_done = false) {
   const Level& L = h->lev[l];
   SweepState st;
+  if (c0_done) st.last = 0;   // colour 0 of the first sweep came with the restriction
   int rc;
   if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
   if (h->pre == 0) {
@@ -778,6 +799,7 @@ static int vcycle_noalloc_t(hpg_problem* h, int l, const T* r, T* z, T* const* c
   const Level& C = h->lev[l + 1];
   T* rc_vec = crhs[l + 1];
   T* zc_vec = csol[l + 1];
+  const bool fuse = l + 1 == h->nlev - 1 || h->pre >= 1;
   const long long cnt = (long long)L.g.cdx[kCoarseColour] * L.g.cdy[kCoarseColour] *
                         L.g.cdz[kCoarseColour];
   const int prec = Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32;
@@ -785,10 +807,11 @@ static int vcycle_noalloc_t(hpg_problem* h, int l, const T* r, T* z, T* const* c
   rc = launch(h, K_RESTRICT, l, prec, cnt * bytes_restrict_row(sizeof(T), sizeof(T)), s,
               "restrict_kernel", [&] {
                 return kl(h, restrict_fn<T>(L), grid_for(cnt, kThreads), kThreads, s, L.g,
-                          C.g, vals, L.cols, r, z, rc_vec);
+                          C.g, vals, L.cols, r, z, rc_vec, fuse ? zc_vec : (T*)nullptr,
+                          Prec<T>::vals(C) + kCentre * C.g.n_store);
               });
   if (rc) return rc;
-  if ((rc = vcycle_noalloc_t<T>(h, l + 1, rc_vec, zc_vec, crhs, csol, s))) return rc;
+  if ((rc = vcycle_noalloc_t<T>(h, l + 1, rc_vec, zc_vec, crhs, csol, s, fuse))) return rc;
   rc = launch(h, K_PROLONG, l, prec, cnt * 3.0 * sizeof(T), s, "prolong_kernel", [&] {
     return kl(h, prolong_kernel<T>, grid_for(cnt, kThreads), kThreads, s, L.g, C.g,
               (const T*)zc_vec, z);
