@@ -300,8 +300,10 @@ int launch_spmv(hpg_problem* h, int level, hpg_prec prec, const void* x, void* y
                 cudaStream_t s);
 int launch_residual64(hpg_problem* h, const double* b, const double* x, double* r,
                       cudaStream_t s);
+// c0_done: z already holds the first sweep's colour-0 phase, z_i = r_i / a_ii
+// on colour block 0 (written by the kernel that produced r).
 int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
-               cudaStream_t s);
+               cudaStream_t s, bool c0_done = false);
 // V-cycle from `level` down in one thread-block cluster; HPG_ERR_UNSUPPORTED
 // when the level is too large or no cluster fits (the caller then launches
 // one kernel per phase).

@@ -609,10 +609,26 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
   }
 }
 
+// The next V-cycle's first phase, done by the kernel that writes its input r:
+// the first forward sweep from zero starts with colour 0, whose rows have no
+// neighbour of a lower colour, so z_i = r_i / a_ii on the colour-0 block
+// [0, c0_rows) (c0_rows = 0: not done).  Same division as the phase.
+template <typename T>
+__device__ __forceinline__ void first_phase4(long long i0, const T (&v)[4], T* __restrict__ z0,
+                                             const T* __restrict__ diag, long long c0_rows) {
+  if (i0 >= c0_rows) return;
+  T d[4], zv[4];
+  Vec4<T>::ld_cs(diag + i0, d);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) zv[r] = v[r] / d[r];
+  Vec4<T>::st(z0 + i0, zv);
+}
+
 // q_new /= beta (the Arnoldi normalisation), beta from the solve state.
 template <typename T>
 __global__ void __launch_bounds__(256)
-arnoldi_scale_kernel(T* __restrict__ qnew, long long ns, const SolveState* st) {
+arnoldi_scale_kernel(T* __restrict__ qnew, long long ns, const SolveState* st,
+                     T* __restrict__ z0, const T* __restrict__ diag, long long c0_rows) {
   pdl_trigger();
   pdl_wait();
   // one FP64 division per block (FP64 throughput is low on this GPU)
@@ -634,6 +650,7 @@ arnoldi_scale_kernel(T* __restrict__ qnew, long long ns, const SolveState* st) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) v[r] = v[r] * inv;
     Vec4<T>::st(qnew + (g << 2), v);
+    first_phase4<T>(g << 2, v, z0, diag, c0_rows);
   }
 }
 
@@ -644,7 +661,8 @@ template <typename B>
 __global__ void __launch_bounds__(256)
 arnoldi_quantize_kernel(const float* __restrict__ wpp, long long ns, B* __restrict__ qnew,
                         float* __restrict__ qf, float* __restrict__ sigma_out,
-                        const SolveState* st) {
+                        const SolveState* st, float* __restrict__ z0,
+                        const float* __restrict__ diag, long long c0_rows) {
   pdl_trigger();
   pdl_wait();
   __shared__ float s_inv_m, s_sigma;
@@ -672,6 +690,7 @@ arnoldi_quantize_kernel(const float* __restrict__ wpp, long long ns, B* __restri
     }
     st_group<B, 4>(qnew + (g << 2), u);
     st_group<float, 4>(qf + (g << 2), v);
+    first_phase4<float>(g << 2, v, z0, diag, c0_rows);
   }
 }
 
@@ -817,7 +836,8 @@ __global__ void __launch_bounds__(256)
 cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q0,
                    float* __restrict__ qf, float* __restrict__ qscale,
                    const double* __restrict__ rho2, double* __restrict__ t, SolveState* st,
-                   const unsigned long long* __restrict__ handles, int nhandles) {
+                   const unsigned long long* __restrict__ handles, int nhandles,
+                   T* __restrict__ z0, const T* __restrict__ diag, long long c0_rows) {
   pdl_trigger();
   pdl_wait();
   // the scalars once per block (one FP64 division each)
@@ -841,12 +861,18 @@ cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q
     if (i < ns) {
       const B u = basis_from<B>((float)(r[i] * inv));
       q0[i] = u;
-      qf[i] = sigma * basis_to(u);
+      const float v = sigma * basis_to(u);
+      qf[i] = v;
+      if (i < c0_rows) z0[i] = v / diag[i];   // the first V-cycle's first phase
     }
     if (i == 0) qscale[0] = sigma;
   } else {
     const double inv = s_inv;
-    if (i < ns) q0[i] = (T)(r[i] * inv);
+    if (i < ns) {
+      const T v = (T)(r[i] * inv);
+      q0[i] = v;
+      if (i < c0_rows) z0[i] = v / diag[i];   // the first V-cycle's first phase
+    }
   }
   if (i == 0) {
     t[0] = rho;
@@ -923,6 +949,20 @@ static int launch_pass(hpg_problem* h, const B* Q, long long ns, int ncol, const
   });
 }
 
+// Rows [0, first_phase_rows) of level 0 (its colour-0 block) whose first
+// V-cycle phase the kernel producing the V-cycle's input writes along with
+// it; 0 when the V-cycle does not start with a sweep from zero there.
+static long long first_phase_rows(const hpg_problem* h) {
+  return (h->pre >= 1 || h->nlev == 1) ? h->lev[0].g.off[1] : 0;
+}
+template <typename T> static const T* level0_diag(const hpg_problem* h);
+template <> const float* level0_diag<float>(const hpg_problem* h) {
+  return h->lev[0].v32 + kCentre * h->lev[0].g.n_store;
+}
+template <> const double* level0_diag<double>(const hpg_problem* h) {
+  return h->lev[0].v64 + kCentre * h->lev[0].g.n_store;
+}
+
 // One inner step k (0-based): z = M^{-1} q_k, w = A z, CGS2 against
 // q_0..q_k, q_{k+1} = w / ||w||, Givens update; `next` opens step k+1.
 // A scaled basis preconditions the dequantised q_k (qf) and quantises
@@ -940,7 +980,8 @@ static int enqueue_step(hpg_problem* h, int k, hpg_prec prec, unsigned long long
   if constexpr (S) r_in = ws->qf;
   else r_in = Q + (long long)k * ns;
   int rc;
-  if ((rc = run_vcycle(h, 0, prec, r_in, z, s))) return rc;
+  // colour 0 of the V-cycle's first sweep came with r_in (first_phase_rows)
+  if ((rc = run_vcycle(h, 0, prec, r_in, z, s, first_phase_rows(h) > 0))) return rc;
   if ((rc = launch_spmv(h, 0, prec, z, w, s))) return rc;
   const int ncol = k + 1;
   B* qnew = Q + (long long)(k + 1) * ns;
@@ -956,13 +997,15 @@ static int enqueue_step(hpg_problem* h, int k, hpg_prec prec, unsigned long long
                   [&] {
                     return kl(h, arnoldi_quantize_kernel<B>, grid_for(ns / 4, 256), 256, s,
                               (const float*)w, ns, qnew, ws->qf, ws->qscale + k + 1,
-                              (const SolveState*)ws->st);
+                              (const SolveState*)ws->st, (float*)z, level0_diag<float>(h),
+                              first_phase_rows(h));
                   });
   } else {
     return launch(h, K_ARNOLDI_SCALE, 0, prec_of<T>(), 2.0 * h->lev[0].n * sizeof(T), s,
                   "arnoldi_scale_kernel", [&] {
                     return kl(h, arnoldi_scale_kernel<T>, grid_for(ns / 4, 256), 256, s, qnew,
-                              ns, (const SolveState*)ws->st);
+                              ns, (const SolveState*)ws->st, z, level0_diag<T>(h),
+                              first_phase_rows(h));
                   });
   }
 }
@@ -1021,7 +1064,8 @@ static int enqueue_cycle_start(hpg_problem* h, const unsigned long long* handles
                 "cycle_start_kernel", [&] {
                   return kl(h, cycle_start_kernel<T, B>, grid_for(ns, 256), 256, s,
                             (const double*)ws->r, ns, (B*)ws->Q, ws->qf, ws->qscale,
-                            (const double*)ws->rho2, ws->t, ws->st, handles, nh);
+                            (const double*)ws->rho2, ws->t, ws->st, handles, nh, (T*)ws->z,
+                            level0_diag<T>(h), first_phase_rows(h));
                 });
 }
 

@@ -681,9 +681,10 @@ static int smooth_t(hpg_problem* h, int level, const T* r, T* z, int sweeps, boo
 }
 
 int run_vcycle(hpg_problem* h, int level, hpg_prec prec, const void* r, void* z,
-               cudaStream_t s) {
-  if (prec == HPG_FP64) return vcycle_t<double>(h, level, (const double*)r, (double*)z, s);
-  return vcycle_t<float>(h, level, (const float*)r, (float*)z, s);
+               cudaStream_t s, bool c0_done) {
+  if (prec == HPG_FP64)
+    return vcycle_t<double>(h, level, (const double*)r, (double*)z, s, c0_done);
+  return vcycle_t<float>(h, level, (const float*)r, (float*)z, s, c0_done);
 }
 
 }  // namespace hpg
