@@ -133,9 +133,14 @@ static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
   }
 }
 
+// Threads per CTA of the latency variant; measured on GB300 at 128^3, the
+// solve took 106.6 / 106.1 / 106.0 / 105.0 / 109.0 ms with 32 / 64 / 128 / 256
+// / 512.
+constexpr int kSmallThreads = 256;
+
 // Latency variant, for coarse levels (matrix resident in L2, at most a few
-// tens of thousands of rows per phase): 64-thread CTAs spread the rows over
-// the SMs, and each thread loads its row's 27 indices and values *before* the
+// tens of thousands of rows per phase): one row per thread, kSmallThreads per
+// CTA, and each thread loads its row's 27 indices and values *before* the
 // programmatic wait -- the matrix does not depend on earlier kernels -- so that
 // latency overlaps the previous phase; after the wait it issues all the
 // gathers of x at once.  Same slot order and arithmetic as gs_phase_kernel.
@@ -144,7 +149,7 @@ static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
 // c the first forward sweep's colour c (slots with a later neighbour colour
 // are neither loaded nor gathered).
 template <typename T, int MODE, int MC>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(kSmallThreads)
 gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                       const T* __restrict__ r, T* x, long long row0, long long nrows,
                       long long valid_end) {
@@ -513,8 +518,9 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                   // the 32768-row level-1 phases overlapped too, the 128^3
                   // solve took 110.3 ms instead of 107.4)
                   if (nrows > kPdlSmallRows) h->pdl_next = false;
-                  return kl(h, gs_small_fn<T>(mat_mode(L), c, from_zero), grid_for(nrows, 64),
-                            64, s, vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                  return kl(h, gs_small_fn<T>(mat_mode(L), c, from_zero),
+                            grid_for(nrows, kSmallThreads), kSmallThreads, s, vals, L.cols,
+                            L.g.n_store, r, z, row0, nrows, valid_end);
                 });
 }
 
