@@ -134,13 +134,16 @@ static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
 }
 
 // Threads per CTA of the latency variant; measured on GB300 at 128^3, the
-// solve took 106.6 / 106.1 / 106.0 / 105.0 / 109.0 ms with 32 / 64 / 128 / 256
-// / 512.
-constexpr int kSmallThreads = 256;
+// FP32 solve took 106.6 / 106.1 / 106.0 / 105.0 / 109.0 ms with 32 / 64 / 128
+// / 256 / 512, while the FP64 solve was 3 % slower with 256 than with 64.
+template <typename T>
+__host__ __device__ constexpr int small_threads() {
+  return sizeof(T) == 4 ? 256 : 64;
+}
 
 // Latency variant, for coarse levels (matrix resident in L2, at most a few
-// tens of thousands of rows per phase): one row per thread, kSmallThreads per
-// CTA, and each thread loads its row's 27 indices and values *before* the
+// tens of thousands of rows per phase): one row per thread, small_threads<T>()
+// per CTA, and each thread loads its row's 27 indices and values *before* the
 // programmatic wait -- the matrix does not depend on earlier kernels -- so that
 // latency overlaps the previous phase; after the wait it issues all the
 // gathers of x at once.  Same slot order and arithmetic as gs_phase_kernel.
@@ -149,7 +152,7 @@ constexpr int kSmallThreads = 256;
 // c the first forward sweep's colour c (slots with a later neighbour colour
 // are neither loaded nor gathered).
 template <typename T, int MODE, int MC>
-__global__ void __launch_bounds__(kSmallThreads)
+__global__ void __launch_bounds__(small_threads<T>())
 gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                       const T* __restrict__ r, T* x, long long row0, long long nrows,
                       long long valid_end) {
@@ -519,8 +522,8 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                   // solve took 110.3 ms instead of 107.4)
                   if (nrows > kPdlSmallRows) h->pdl_next = false;
                   return kl(h, gs_small_fn<T>(mat_mode(L), c, from_zero),
-                            grid_for(nrows, kSmallThreads), kSmallThreads, s, vals, L.cols,
-                            L.g.n_store, r, z, row0, nrows, valid_end);
+                            grid_for(nrows, small_threads<T>()), small_threads<T>(), s, vals,
+                            L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
                 });
 }
 
