@@ -95,3 +95,28 @@ def test_gs_traffic_only_for_unchanged_kernel_sources(monkeypatch):
     assert bench.gs_traffic("mxp_gmres50_320cube") is None
     monkeypatch.setitem(bench.GS_TRAFFIC, "bytes_per_launch", None)
     assert bench.gs_traffic() is None
+
+
+def test_gs_kernel_text_blocks_found(tmp_path, monkeypatch):
+    # the hash covers the kernel and the helpers it inlines; each block must be
+    # found, and an edit inside one changes the hash while one outside does not
+    import bench
+    sha = bench.gs_sources_sha256()
+    assert sha is not None and len(sha) == 64
+    for rel, start, end in bench.GS_KERNEL_TEXT:
+        text = open(os.path.join(ROOT, rel)).read()
+        i = text.find(start)
+        assert i >= 0 and text.find(end, i + len(start)) > i
+    rel, start, _ = bench.GS_KERNEL_TEXT[0]
+    text = open(os.path.join(ROOT, rel)).read()
+    (tmp_path / "paper_2507_11512_gb300" / "csrc").mkdir(parents=True)
+    for r, _, _ in bench.GS_KERNEL_TEXT:
+        dst = tmp_path / r
+        if not dst.exists():
+            dst.write_text(open(os.path.join(ROOT, r)).read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / rel).write_text("// an edit outside the kernel\n" + text)
+    assert bench.gs_sources_sha256() == sha
+    i = text.find(start) + len(start)
+    (tmp_path / rel).write_text(text[:i] + "\n// an edit inside the kernel" + text[i:])
+    assert bench.gs_sources_sha256() != sha
