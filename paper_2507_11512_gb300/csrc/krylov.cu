@@ -919,8 +919,7 @@ static int pass_grid(hpg_problem* h) {
 
 template <typename T, typename B, int KMAX, int KIND>
 static cudaError_t enqueue_pass(hpg_problem* h, const B* Q, long long ns, int ncol, const T* w,
-                                T* wout, double* out, int k, unsigned long long next,
-                                cudaStream_t s) {
+                                T* wout, double* out, unsigned long long next, cudaStream_t s) {
   Workspace* ws = h->ws;
   return kl(h, cgs2_pass_kernel<T, B, KMAX, KIND>, pass_grid<T, B, KMAX, KIND>(h), kRedThreads,
             s, Q, ns, ncol, w, (const float*)ws->qscale, (const double*)ws->h1,
@@ -938,14 +937,13 @@ static int launch_pass(hpg_problem* h, const B* Q, long long ns, int ncol, const
   // Q columns + w (+ the w' / w'' write)
   const double bytes = (double)h->lev[0].n *
                        (ncol * (double)sizeof(B) + (KIND == kGemvT ? 1.0 : 2.0) * sizeof(T));
-  const int k = ncol - 1;
   return launch(h, cls[KIND], 0, prec_of<T>(), bytes, s, "cgs2_pass_kernel", [&] {
-    if (ncol <= 8) return enqueue_pass<T, B, 8, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
+    if (ncol <= 8) return enqueue_pass<T, B, 8, KIND>(h, Q, ns, ncol, w, wout, out, next, s);
     if (ncol <= 16)
-      return enqueue_pass<T, B, 16, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
+      return enqueue_pass<T, B, 16, KIND>(h, Q, ns, ncol, w, wout, out, next, s);
     if (ncol <= 32)
-      return enqueue_pass<T, B, 32, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
-    return enqueue_pass<T, B, 64, KIND>(h, Q, ns, ncol, w, wout, out, k, next, s);
+      return enqueue_pass<T, B, 32, KIND>(h, Q, ns, ncol, w, wout, out, next, s);
+    return enqueue_pass<T, B, 64, KIND>(h, Q, ns, ncol, w, wout, out, next, s);
   });
 }
 
