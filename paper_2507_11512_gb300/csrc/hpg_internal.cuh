@@ -77,8 +77,9 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
 
-// Matrix load of a level: streamed (evict-first) on levels larger than L2,
-// cached normally on coarse levels, which every sweep reads again.
+// Matrix load of the bandwidth-variant kernels: streamed (evict-first), or
+// cached normally where the slice is read again soon (a streamed level's
+// kept colour phases, levels below the streaming size).
 template <bool STREAM, typename V>
 __device__ __forceinline__ V ld_matrix(const V* p) {
   if (STREAM) return __ldcs(p);
