@@ -406,3 +406,37 @@ def test_theta_scaled_diagonal_matches_brute_force():
     np.testing.assert_array_equal(A, A_dense)
     lv = O.build_hierarchy(4, 4, 4, 2, 0.0, rng.uniform(0.9, 1.1, 64))
     np.testing.assert_array_equal(lv[1].theta, lv[0].theta[lv[0].fc])
+
+
+# ------------------------------------------------------- spectral closed form --
+@pytest.mark.parametrize("dims", [(6, 6, 6), (5, 3, 4)])
+def test_spectrum_matches_kronecker_closed_form(dims):
+    """beta = 0: the truncated 27-point operator is 27 I - J_x (x) J_y (x) J_z
+    with J_n = tridiag(1, 1, 1) of order n (J's diagonal gives the centre
+    1*1*1 = 1, its off-diagonals every neighbour), whose eigenvalues are
+    1 + 2 cos(pi k / (n + 1)), k = 1..n.  So the spectrum of A is
+    {27 - prod_d (1 + 2 cos(pi k_d / (n_d + 1)))}: every value and every
+    boundary truncation of the oracle's matrix enters it."""
+    nx, ny, nz = dims
+    A = O.build_matrix(nx, ny, nz, 0.0).toarray()
+    ev = np.sort(np.linalg.eigvalsh(A))
+    j = [1.0 + 2.0 * np.cos(np.pi * np.arange(1, n + 1) / (n + 1)) for n in (nx, ny, nz)]
+    ref = np.sort((27.0 - np.einsum("i,j,k->ijk", j[0], j[1], j[2])).ravel())
+    np.testing.assert_allclose(ev, ref, rtol=0, atol=1e-12)
+
+
+def test_theta_scaled_operator_nonsingular_12cube():
+    """The differentiable-solve operator (a_ii = 26 theta_i, theta ~ U(0.9, 1.1),
+    beta = 0.5) has rows that are not diagonally dominant; its 12^3 instance is
+    checked by a dense SVD (LAPACK): smallest singular value well away from 0,
+    close to the smallest eigenvalue 27 - (1 + 2 cos(pi/13))^3 = 1.539 of the
+    unperturbed symmetric operator; the transpose has the same singular values."""
+    rng = np.random.default_rng(0)
+    theta = rng.uniform(0.9, 1.1, 12 ** 3)
+    A = O.build_matrix(12, 12, 12, 0.5, theta).toarray()
+    s = np.linalg.svd(A, compute_uv=False)
+    lam0 = 27.0 - (1.0 + 2.0 * np.cos(np.pi / 13.0)) ** 3
+    assert 0.5 * lam0 < s[-1] < 2.0 * lam0
+    assert s[0] / s[-1] < 100.0
+    At = O.build_matrix(12, 12, 12, -0.5, theta).toarray()
+    np.testing.assert_array_equal(At, A.T)
