@@ -110,3 +110,46 @@ def test_single_gram_schmidt_pass_changes_basis_orthogonality_bound():
         Q.append(w / np.linalg.norm(w))
     Qm = np.column_stack(Q)
     assert np.abs(Qm.T @ Qm - np.eye(len(Q))).max() > 1e-13
+
+
+def spectrum_matches(dims=(5, 3, 4)):
+    nx, ny, nz = dims
+    A = O.build_matrix(nx, ny, nz, 0.0).toarray()
+    ev = np.sort(np.linalg.eigvalsh(A))
+    j = [1.0 + 2.0 * np.cos(np.pi * np.arange(1, n + 1) / (n + 1)) for n in (nx, ny, nz)]
+    ref = np.sort((27.0 - np.einsum("i,j,k->ijk", j[0], j[1], j[2])).ravel())
+    return np.allclose(ev, ref, rtol=0, atol=1e-12)
+
+
+def test_periodic_wrap_instead_of_truncation_is_caught(monkeypatch):
+    real_index = O.natural_index
+    dims = (5, 3, 4)
+
+    def wrapped(i, j, k, nx, ny):
+        return real_index(np.mod(i, nx), np.mod(j, ny), np.mod(k, dims[2]), nx, ny)
+
+    def bad(nx, ny, nz, beta=0.0, theta=None):
+        # every neighbour kept, out-of-grid ones wrapped around (a torus)
+        n = nx * ny * nz
+        ii, jj, kk = O.grid_coords(nx, ny, nz)
+        A = np.zeros((n, n))
+        for (dx, dy, dz) in O.STENCIL_OFFSETS:
+            c = wrapped(ii + dx, jj + dy, kk + dz, nx, ny)
+            v = 26.0 if (dx, dy, dz) == (0, 0, 0) else O.off_diagonal_value(dx, dy, dz, beta)
+            np.add.at(A, (np.arange(n), c), v)
+        import scipy.sparse as sp
+        return sp.csr_matrix(A)
+    assert spectrum_matches(dims)
+    monkeypatch.setattr(O, "build_matrix", bad)
+    assert not spectrum_matches(dims)
+
+
+def test_diagonal_off_by_one_is_caught(monkeypatch):
+    real = O.build_matrix
+
+    def bad(nx, ny, nz, beta=0.0, theta=None):
+        A = real(nx, ny, nz, beta, theta).tolil()
+        A.setdiag(A.diagonal() + 1.0)                # 27 instead of 26
+        return A.tocsr()
+    monkeypatch.setattr(O, "build_matrix", bad)
+    assert not spectrum_matches()
