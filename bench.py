@@ -233,7 +233,6 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU arm
 def run_gpu(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 

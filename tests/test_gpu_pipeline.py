@@ -2,7 +2,6 @@
 streams from memory: bitwise equal to the phase-by-phase sweep in the
 smoother, the V-cycle and whole solves, over repeated launches."""
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -6,7 +6,6 @@ term, a flipped sign, a wrong index) and checks that the independent pin of
 """
 
 import numpy as np
-import pytest
 import scipy.linalg as sla
 
 from oracle import hpg_oracle as O

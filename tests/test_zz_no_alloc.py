@@ -8,8 +8,6 @@ shared array keeps the previous call's contents).  This file is collected
 last on purpose, and it also passes when run alone.
 """
 
-import ctypes
-
 import numpy as np
 import pytest
 
