@@ -152,3 +152,27 @@ def test_diagonal_off_by_one_is_caught(monkeypatch):
         return A.tocsr()
     monkeypatch.setattr(O, "build_matrix", bad)
     assert not spectrum_matches()
+
+
+def test_stencil_row_mistakes_are_caught(monkeypatch):
+    from tests.test_oracle_pins import stencil_row_dense
+    dims, beta = (4, 3, 4), 0.5
+    theta = np.linspace(0.9, 1.1, 48)
+    A, pts = dense_stencil(*dims, beta, theta)
+
+    def matches():
+        return all(np.array_equal(stencil_row_dense(*dims, i, j, k, beta, theta[q]), A[q])
+                   for q, (i, j, k) in enumerate(pts))
+
+    assert matches()
+    good = O.off_diagonal_value
+    # the perturbation taken from the row's point of view (d = x_i - x_j)
+    monkeypatch.setattr(O, "off_diagonal_value", lambda dx, dy, dz, b: good(-dx, -dy, -dz, b))
+    assert not matches()
+    monkeypatch.setattr(O, "off_diagonal_value", good)
+    # y and z strides swapped in the natural index
+    good_idx = O.natural_index
+    monkeypatch.setattr(O, "natural_index", lambda i, j, k, nx, ny: i + ny * (j + nx * k))
+    assert not matches()
+    monkeypatch.setattr(O, "natural_index", good_idx)
+    assert matches()

@@ -440,3 +440,51 @@ def test_theta_scaled_operator_nonsingular_12cube():
     assert s[0] / s[-1] < 100.0
     At = O.build_matrix(12, 12, 12, -0.5, theta).toarray()
     np.testing.assert_array_equal(At, A.T)
+
+
+# ------------------------------------------------------------ single rows --
+def stencil_row_dense(nx, ny, nz, i, j, k, beta, theta_ijk):
+    """stencil_row as a dense row vector (natural order)."""
+    out = np.zeros(nx * ny * nz)
+    for c, v in O.stencil_row(nx, ny, nz, i, j, k, beta, theta_ijk):
+        assert out[c] == 0.0, "column listed twice"
+        out[c] = v
+    return out
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4), (5, 3, 4), (1, 2, 3), (3, 1, 1)])
+@pytest.mark.parametrize("beta", [0.0, 0.5, -0.75])
+def test_stencil_row_matches_brute_force_every_point(dims, beta):
+    # every point of small grids (interior, faces, edges, corners) against the
+    # all-pairs construction, with a per-cell diagonal scale theta != 1
+    theta = np.random.default_rng(3).uniform(0.9, 1.1, dims[0] * dims[1] * dims[2])
+    A, pts = dense_stencil(*dims, beta, theta)
+    for q, (i, j, k) in enumerate(pts):
+        row = stencil_row_dense(*dims, i, j, k, beta, theta[q])
+        np.testing.assert_array_equal(row, A[q])
+
+
+def test_stencil_row_matches_matrix_rows_on_a_larger_grid():
+    # the rows the full-size GPU tests sample (corners, faces, edges, random
+    # interior points) on a grid too large for a dense matrix
+    dims, beta = (33, 17, 24), 0.5
+    nx, ny, nz = dims
+    theta = np.random.default_rng(4).uniform(0.9, 1.1, nx * ny * nz)
+    A = O.build_matrix(*dims, beta, theta).tocsr()
+    rng = np.random.default_rng(5)
+    pts = [tuple(int(v) for v in rng.integers(0, (nx, ny, nz))) for _ in range(200)]
+    pts += [(a, b, c) for a in (0, nx - 1) for b in (0, ny - 1) for c in (0, nz - 1)]
+    pts += [(0, 5, 7), (nx - 1, 5, 7), (4, 0, 7), (4, ny - 1, 7), (4, 5, 0), (4, 5, nz - 1),
+            (0, 0, 9), (nx - 1, ny - 1, 9), (0, 8, nz - 1), (16, 0, 0)]
+    for (i, j, k) in pts:
+        q = O.natural_index(i, j, k, nx, ny)
+        row = O.stencil_row(nx, ny, nz, i, j, k, beta, theta[q])
+        ref = A.getrow(q)
+        assert sorted(c for c, _ in row) == sorted(ref.indices.tolist())
+        got = dict(row)
+        for c, v in zip(ref.indices, ref.data):
+            assert got[c] == v
+        # the row's length is the product of the in-grid neighbours per axis
+        per_axis = [sum(1 for d in (-1, 0, 1) if 0 <= p + d < n)
+                    for p, n in zip((i, j, k), dims)]
+        assert len(row) == per_axis[0] * per_axis[1] * per_axis[2]
