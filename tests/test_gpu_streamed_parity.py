@@ -1,0 +1,159 @@
+"""Oracle parity at the sizes whose matrices stream from HBM.
+
+On a level whose FP32 ELL arrays (27 slots x (4-byte value + 4-byte index)
+per storage row) exceed 96 MiB, the library runs its bandwidth kernels:
+the streamed Gauss-Seidel colour phase (every slot, and the first forward
+sweep's per-colour slot sets), the phases that keep their matrix slice in L2
+(colour 6 forward, colour 0 last, where a slice fits in 96 MiB), and the
+streamed fused residual-restriction.  The small-grid parity tests never reach
+those kernels, so these tests compare them with the FP64 oracle element by
+element at grids from 80^3 to 160^3, in the launch configuration of the
+128^3 benchmark solve:
+
+* hpg_mg_smooth (eqs. (1)-(2), Sec. 3.2.1): 1 and 2 sweeps from z = 0 and one
+  from a given iterate, against the oracle's colour phases;
+* hpg_mg_vcycle (Fig. 1, Sec. 3.2.4) from every level, against the oracle's
+  V-cycle;
+* GMRES-IR (Algorithm 3) to 1e-12, against the oracle's solution: the kernels
+  that write the V-cycle's input (cycle start, Arnoldi scaling, the 2-byte
+  basis quantisation) also run the first colour phase of level 0 there.
+
+Tolerances: FP64 1e-13 relative in the max norm, FP32 1e-6 relative in the
+2-norm (per smoother or V-cycle call); solves 1e-8 relative after refinement.
+FP32 inputs are drawn and rounded before both sides see them.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2507_11512_gb300 as hpg  # noqa: E402
+from oracle import hpg_oracle as O  # noqa: E402
+from tests.gpu_helpers import (FP32_REL, FP64_REL, oracle_hierarchy, to_natural,  # noqa: E402
+                               to_storage)
+from workloads import random_vector, rhs_noise, x_true  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+BETA = 0.5
+STREAM_BYTES = 96 << 20   # FP32 ELL bytes above which a level's matrix streams
+KEEP_SLICE_BYTES = 96 << 20   # a colour slice kept in L2 must fit in this
+
+# 80^3: smallest cube that streams; 82 x 78 x 84: odd colour-block extents and
+# ragged 32-row padding (two levels); 128^3: the benchmark grid; 160^3: level 0
+# slices too large to keep (the 320^3 configuration) and level 1 streamed too
+GRIDS = [(80, 80, 80), (82, 78, 84), (128, 128, 128), (160, 160, 160)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def streamed(info):
+    return info["n_store"] * 27 * 8 > STREAM_BYTES
+
+
+def max_slice_bytes(info):
+    cnt = [info["colour_offset"][c + 1] - info["colour_offset"][c] for c in range(8)]
+    return max(cnt) * 27 * 8
+
+
+def close(z, ref, dtype):
+    if dtype == torch.float64:
+        return np.abs(z - ref).max() <= FP64_REL * np.abs(ref).max()
+    return np.linalg.norm(z - ref) <= FP32_REL * np.linalg.norm(ref)
+
+
+def npdtype(dtype):
+    return np.float64 if dtype == torch.float64 else np.float32
+
+
+def test_grids_take_the_streamed_branches():
+    """The grids above reach the kernels this file is about."""
+    seen_keep, seen_nokeep, seen_streamed_coarse = False, False, False
+    for dims in GRIDS:
+        with hpg.Problem(*dims, beta=BETA) as p:
+            assert streamed(p.info[0]), dims
+            if max_slice_bytes(p.info[0]) <= KEEP_SLICE_BYTES:
+                seen_keep = True
+            else:
+                seen_nokeep = True
+            if p.levels > 1 and streamed(p.info[1]):
+                seen_streamed_coarse = True
+    assert seen_keep and seen_nokeep and seen_streamed_coarse
+
+
+@pytest.mark.parametrize("dims", GRIDS)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_streamed_smooth_matches_oracle(dims, dtype):
+    lv = oracle_hierarchy(dims, 4, BETA)
+    with hpg.Problem(*dims, beta=BETA, levels=4) as p:
+        for l, L in enumerate(lv):
+            if not streamed(p.info[l]):
+                continue
+            r = random_vector(L.n, seed=61 + l, dtype=npdtype(dtype)).astype(np.float64)
+            z0 = random_vector(L.n, seed=71 + l, dtype=npdtype(dtype)).astype(np.float64)
+            rt = torch.tensor(to_storage(r, L.dims), dtype=dtype, device=DEV)
+            for sweeps, zero in [(1, True), (2, True), (1, False)]:
+                if zero:
+                    # z enters as 0 and is never read: NaN rows prove it
+                    zt = torch.tensor(to_storage(np.full(L.n, np.nan), L.dims), dtype=dtype,
+                                      device=DEV)
+                    ref = np.zeros(L.n)
+                else:
+                    zt = torch.tensor(to_storage(z0, L.dims), dtype=dtype, device=DEV)
+                    ref = z0.copy()
+                hpg.mg_smooth(p.h, l, rt, zt, sweeps, zero)
+                for _ in range(sweeps):
+                    O.symgs(L, r, ref)
+                z = to_natural(zt.cpu().numpy(), L.dims).astype(np.float64)
+                assert np.isfinite(z).all()
+                assert close(z, ref, dtype), (dims, l, sweeps, zero)
+
+
+@pytest.mark.parametrize("dims", GRIDS)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_streamed_vcycle_matches_oracle(dims, dtype):
+    lv = oracle_hierarchy(dims, 4, BETA)
+    with hpg.Problem(*dims, beta=BETA, levels=4) as p:
+        assert p.levels == len(lv)
+        for l, L in enumerate(lv):
+            r = random_vector(L.n, seed=81 + l, dtype=npdtype(dtype)).astype(np.float64)
+            rt = torch.tensor(to_storage(r, L.dims), dtype=dtype, device=DEV)
+            z = to_natural(p.vcycle(rt, level=l).cpu().numpy(), L.dims).astype(np.float64)
+            ref = O.vcycle(lv, r, l)
+            assert close(z, ref, dtype), (dims, l)
+
+
+def solve_vs_oracle(dims, basis):
+    lv = oracle_hierarchy(dims, 4, BETA)
+    n = lv[0].n
+    b = lv[0].A @ x_true(n) + rhs_noise(n, 1e-3, seed=0)
+    x_o, info_o = O.gmres_ir(lv, b, tol=1e-12, restart=30)
+    with hpg.Problem(*dims, beta=BETA, levels=4) as p:
+        assert streamed(p.info[0])
+        bt = torch.tensor(b, device=DEV)
+        xt = torch.zeros_like(bt)
+        info = hpg.gmres_ir_solve(p.h, bt, xt, tol=1e-12, restart=30, inner=hpg.HPG_FP32,
+                                  basis=basis)
+        x = xt.cpu().numpy()
+    assert info["status"] == 0 and info["converged"] == 1
+    assert np.linalg.norm(b - lv[0].A @ x) / np.linalg.norm(b) < 1e-12
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= 1e-8
+    assert info["iterations"] <= 1.5 * info_o.iterations + 5
+
+
+@pytest.mark.parametrize("basis", [hpg.HPG_FP32, hpg.HPG_BF16])
+def test_streamed_mxp_solve_80cube_matches_oracle(basis):
+    solve_vs_oracle((80, 80, 80), basis)
+
+
+@pytest.mark.slow
+def test_streamed_mxp_solve_128cube_matches_oracle():
+    """The benchmark grid and solver settings, to 1e-12 against the oracle."""
+    solve_vs_oracle((128, 128, 128), hpg.HPG_FP32)
