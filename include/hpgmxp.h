@@ -119,7 +119,9 @@ HPG_API int hpg_setup_problem(int nx, int ny, int nz,
  * times 2 divides nx, ny and nz together), each coarse level re-discretising
  * the stencil on the 2x coarser grid; pre/post = symmetric Gauss-Seidel sweeps
  * before/after the coarse correction (>= 0; the coarsest level always does
- * one sweep).  May be called again to rebuild.  Synchronous. */
+ * one sweep).  May be called again to rebuild (this drops the batch buffers
+ * and tuned shapes of the many-right-hand-side entry points; HPG_ERR_STATE
+ * while a multi-system batch uses the problem).  Synchronous. */
 HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels,
                                    int pre_sweeps, int post_sweeps);
 
@@ -178,8 +180,10 @@ HPG_API int hpg_mg_smooth(hpg_problem_t* h, int level, hpg_prec prec,
  * point for callers that cannot allocate device memory when they call --
  * code running inside a CUDA stream capture (cudaMalloc is not allowed there),
  * real-time loops that must not stall on the allocator, or memory-pool owners
- * that forbid allocations outside their pool.  It computes exactly what
- * hpg_mg_vcycle computes (same kernels, same order, same results), but the
+ * that forbid allocations outside their pool.  It computes what hpg_mg_vcycle
+ * computes with one kernel launch per colour phase and transfer (the same
+ * kernels, order and results as hpg_mg_vcycle with the default options; it
+ * ignores HPG_OPT_COARSE_CLUSTER and always launches the phases), but the
  * coarse levels' work vectors (restricted residuals and corrections of levels
  * level+1 .. last) live in one static device array of
  * HPG_NOALLOC_SCRATCH_BYTES bytes that the library declares at file scope:
@@ -195,7 +199,9 @@ HPG_API int hpg_mg_smooth(hpg_problem_t* h, int level, hpg_prec prec,
  *   cudaMemsetAsync on `stream`.
  * - The first call on a device looks up the array's device address once
  *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.
+ *   before any stream capture.  The address is kept for the life of the
+ *   process: a device reset (cudaDeviceReset) before a later call is not
+ *   supported.
  * - All calls share the one array: calls that overlap on the GPU (other
  *   streams, other threads, other handles) race on it and give wrong results.
  * Asynchronous on `stream`. */
@@ -210,7 +216,7 @@ HPG_API int hpg_mg_vcycle_noalloc(hpg_problem_t* h, int level, hpg_prec prec,
  * precision of the V-cycle and the Arnoldi SpMV; `basis` the storage of the
  * Krylov basis Q: HPG_FP64 with inner = HPG_FP64 (plain FP64 GMRES,
  * Algorithm 2), or with inner = HPG_FP32 one of HPG_FP32, HPG_BF16, HPG_FP16.
- * A BF16/FP16 basis (the low-precision basis of Sec. 6's outlook) stores each
+ * A BF16/FP16 basis (the low-precision basis of Sec. 5's outlook) stores each
  * vector as u_j = q_j / max_i |q_ij| with one FP32 scale sigma_j =
  * max_i |q_ij| (so q_j = sigma_j u_j, |u_j| <= 1: no overflow, no vector
  * flushed to zero); CGS2 reads it with FP32 arithmetic, the V-cycle is
@@ -297,7 +303,9 @@ HPG_API int hpg_batch_tune(hpg_problem_t* h, int nrhs, void* stream);
  * solves of the same problems with another nrhs or restart are refused).
  * hpg_batch_solve: B[i], X[i] as for hpg_gmres_ir_solve_batch for problem
  * i; infos: NULL or nsys * nrhs entries (problem-major).  hpg_batch_destroy
- * releases the graph (the problems stay). */
+ * releases the graph (the problems stay).  Destroy a batch before any of its
+ * problems: while it exists, hpg_destroy, hpg_build_mg_hierarchy and
+ * hpg_set_option on those problems return HPG_ERR_STATE. */
 typedef struct hpg_batch hpg_batch_t;
 HPG_API int hpg_batch_create(hpg_problem_t* const* hs, int nsys, int nrhs, int restart,
                              hpg_batch_t** out);
@@ -365,8 +373,10 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
  * that runs out makes the solve return HPG_ERR_TIMEOUT) instead of one launch
  * per colour phase; same results.  0: never; 1 (default): FP64 sweeps only
  * (measured faster on GB300 for FP64, slower for FP32); 2: always.  Setting
- * an option drops captured solve graphs.
- * HPG_ERR_INVALID for an unknown option. */
+ * an option drops captured solve graphs (single- and many-right-hand-side).
+ * HPG_ERR_INVALID for an unknown option; HPG_ERR_STATE while a multi-system
+ * batch uses the problem (its graph keeps the options it was captured
+ * with: destroy the batch, set the option, create it again). */
 #define HPG_OPT_COARSE_CLUSTER 1
 #define HPG_OPT_PDL 2
 #define HPG_OPT_GS_PIPELINE 3
@@ -383,7 +393,9 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);
  * Synchronous. */
 HPG_API int hpg_inject_stall(hpg_problem_t* h, int level, int tiles);
 
-/* Frees everything the handle owns (NULL is accepted). */
+/* Frees everything the handle owns (NULL is accepted).  A problem that a
+ * multi-system batch still uses (hpg_batch_create) is not freed: the call
+ * returns HPG_ERR_STATE; destroy the batch first (hpg_batch_destroy). */
 HPG_API int hpg_destroy(hpg_problem_t* h);
 
 /* Static string naming a status code. */

@@ -113,6 +113,8 @@ class BatchSolver:
         return dict(zip(cand, list(times)[:len(cand)]))
 
     def close(self):
+        """Releases the batch's graph.  Close a BatchSolver before its
+        Problems: the library refuses to destroy a problem a batch uses."""
         if self.b:
             load().hpg_batch_destroy(self.b)
             self.b = None
@@ -122,6 +124,12 @@ class BatchSolver:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def main(argv=None):

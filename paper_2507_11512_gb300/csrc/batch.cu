@@ -298,6 +298,17 @@ struct BatchSpace {
 
 constexpr int kBatchPartStride = (kMaxRestart + 1) * kMaxR;
 
+int batch_owners(const hpg_problem* h) { return h->batch ? h->batch->owners : 0; }
+
+void drop_batch_graph(hpg_problem* h) {
+  BatchSpace* bs = h->batch;
+  if (!bs) return;
+  if (bs->exec) cudaGraphExecDestroy(bs->exec);
+  if (bs->graph) cudaGraphDestroy(bs->graph);
+  bs->exec = nullptr;
+  bs->graph = nullptr;
+}
+
 void destroy_batch(hpg_problem* h) {
   BatchSpace* bs = h->batch;
   if (!bs) return;

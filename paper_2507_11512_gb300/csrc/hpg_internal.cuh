@@ -314,6 +314,10 @@ int launch_permute(hpg_problem* h, int level, int direction, hpg_prec in_prec,
                    const void* in, hpg_prec out_prec, void* out, cudaStream_t s);
 void destroy_workspace(hpg_problem* h);
 void destroy_batch(hpg_problem* h);
+// Multi-system batches (hpg_batch_t) whose graph uses h's batch buffers.
+int batch_owners(const hpg_problem* h);
+// Drops h's captured multi-right-hand-side solve graph (recaptured on use).
+void drop_batch_graph(hpg_problem* h);
 
 inline size_t prec_size(hpg_prec p) {
   switch (p) {

@@ -359,9 +359,15 @@ HPG_API int hpg_build_mg_hierarchy(hpg_problem_t* h, int levels, int pre_sweeps,
               kMaxLevels, pre_sweeps, post_sweeps);
     return HPG_ERR_INVALID;
   }
+  if (batch_owners(h) > 0) {
+    set_error("hpg_build_mg_hierarchy: %d multi-system batch(es) still use this problem; "
+              "destroy them first", batch_owners(h));
+    return HPG_ERR_STATE;
+  }
   h->pdl_next = false;
-  // drop a previous hierarchy (keep level 0's matrix)
+  // drop a previous hierarchy (keep level 0's matrix) and everything sized by it
   destroy_workspace(h);
+  destroy_batch(h);
   for (int l = 0; l < h->nlev; ++l) free_level(h->lev[l], l == 0);
   h->nlev = 1;
   h->hierarchy = false;
@@ -463,6 +469,12 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
     set_error("hpg_set_option: NULL handle");
     return HPG_ERR_INVALID;
   }
+  if (batch_owners(h) > 0) {
+    // a batch's captured graph embeds the current choices
+    set_error("hpg_set_option: %d multi-system batch(es) use this problem; destroy them "
+              "first", batch_owners(h));
+    return HPG_ERR_STATE;
+  }
   switch (option) {
     case HPG_OPT_COARSE_CLUSTER: h->coarse_cluster = value != 0; break;
     case HPG_OPT_PDL: h->pdl_enabled = value != 0; break;
@@ -478,6 +490,7 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
       return HPG_ERR_INVALID;
   }
   if (h->ws) destroy_workspace(h);   // captured graphs embed the old choice
+  drop_batch_graph(h);
   return HPG_OK;
 }
 
@@ -493,6 +506,12 @@ HPG_API int hpg_inject_stall(hpg_problem_t* h, int level, int tiles) {
 
 HPG_API int hpg_destroy(hpg_problem_t* h) {
   if (!h) return HPG_OK;
+  if (batch_owners(h) > 0) {
+    // the batch's graph points at this problem's buffers
+    set_error("hpg_destroy: %d multi-system batch(es) still use this problem; call "
+              "hpg_batch_destroy first", batch_owners(h));
+    return HPG_ERR_STATE;
+  }
   destroy_workspace(h);
   destroy_batch(h);
   destroy_profiler(h);

@@ -168,3 +168,36 @@ def test_batch_invalid_arguments():
             batch.set_shape(p.h, 0, 0, 4, 1, 100)
         with pytest.raises(hpg.HpgError):
             batch.BatchSolver([p, p], 4, tune_shapes=False)
+
+
+def test_problem_outlives_its_batch():
+    """A batch's graph points at its problems' buffers: while it exists the
+    library refuses to destroy, rebuild or re-option those problems; after
+    hpg_batch_destroy the same calls succeed and batched solves still work."""
+    lib = hpg.load()
+    pa, pb = hpg.Problem(16, 16, 16, beta=0.5), hpg.Problem(8, 8, 8, beta=0.25)
+    try:
+        solver = batch.BatchSolver([pa, pb], 2, restart=10)
+        Bs = [torch.ones(2, 16 ** 3, dtype=torch.float64, device=DEV),
+              torch.ones(2, 8 ** 3, dtype=torch.float64, device=DEV)]
+        Xs = [torch.zeros_like(b) for b in Bs]
+        ref = solver.solve(Bs, Xs, tol=1e-8)
+        assert lib.hpg_destroy(pa.h) == hpg.HPG_ERR_STATE
+        assert b"hpg_batch_destroy" in lib.hpg_last_error()
+        assert lib.hpg_build_mg_hierarchy(pb.h, 4, 1, 1) == hpg.HPG_ERR_STATE
+        assert lib.hpg_set_option(pa.h, hpg.HPG_OPT_PDL, 0) == hpg.HPG_ERR_STATE
+        # the refused calls changed nothing: the batch solves as before
+        for x in Xs:
+            x.zero_()
+        again = solver.solve(Bs, Xs, tol=1e-8)
+        assert [[i["iterations"] for i in s] for s in again] == \
+            [[i["iterations"] for i in s] for s in ref]
+        solver.close()
+        hpg.set_option(pa.h, hpg.HPG_OPT_PDL, 0)
+        hpg.build_mg_hierarchy(pb.h, 4, 1, 1)
+        x = torch.zeros_like(Bs[1])
+        infos = batch.solve_batch(pb.h, Bs[1], x, tol=1e-8, restart=10)
+        assert all(i["converged"] for i in infos)
+    finally:
+        pa.close()
+        pb.close()
