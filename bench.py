@@ -32,9 +32,9 @@ METRIC = "GMRES-IR GFLOP/s and time-to-1e-9 residual, MxP vs FP64, 1 GB300; % HB
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes (read + write) per launch of the level-0 FP32 Gauss-Seidel phase
-# kernel at 128^3, from one ncu capture (profiles/gs_phase_level0_128cube.md),
-# valid while the kernel's source text (the kernel and the helpers it
-# inlines) hashes to `sources_sha256`.
+# kernel at 128^3, from one ncu capture of that kernel, valid while the
+# kernel's source text (the kernel and the helpers it inlines) hashes to
+# `sources_sha256`.
 GS_TRAFFIC = {"workload": "mxp_gmres30_128cube", "bytes_per_launch": 65260544.0,
               "sources_sha256": "be7a8b35e8d1a3a25d975a4e6077c2f46a04750886dc46d82ca8dfe415cc897b"}
 # (file, first line of the block, text that ends it): the kernel's source
@@ -166,9 +166,11 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_sample(workload_name, iters):
+def oracle_sample(workload_name, iters, threads=1):
     """Times the FP64 CPU oracle on a bounded sample of the workload in a
-    child process (single-threaded BLAS): `iters` inner GMRES steps."""
+    child process: `iters` inner GMRES steps (or the whole solve, if it takes
+    fewer), with `threads` BLAS threads (None: the library's default, all
+    cores)."""
     code = r"""
 import json, os, sys, time
 sys.path.insert(0, %r)
@@ -193,7 +195,10 @@ print(json.dumps({"seconds": t2 - t1, "setup_s": t1 - t0, "flops": fl,
 """ % (ROOT, workload_name, iters)
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
+        if threads is None:
+            env.pop(k, None)
+        else:
+            env[k] = str(threads)
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=1800)
     if p.returncode != 0:
@@ -229,6 +234,17 @@ def run_reference(args):
             "e2e": {"value": gfl, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def rounded(v, digits=5):
+    """Floats rounded to `digits` significant digits (a shorter JSON line)."""
+    if isinstance(v, float):
+        return float("%.*g" % (digits, v))
+    if isinstance(v, dict):
+        return {k: rounded(x, digits) for k, x in v.items()}
+    if isinstance(v, list):
+        return [rounded(x, digits) for x in v]
+    return v
 
 
 # ------------------------------------------------------------------- GPU arm
@@ -342,50 +358,69 @@ def run_gpu(args):
 
     # ---- dominant kernel (level-0 FP32 Gauss-Seidel phase) timed with CUDA
     # events on the launching stream, launched exactly as the V-cycle launches
-    # it: hpg_mg_smooth = 15 colour phases per sweep (colours 0..7, 6..0),
-    # captured in a CUDA graph like the solve's own launches
+    # it: hpg_mg_smooth = 15 colour phases per sweep (colours 0..7, 6..0).
+    # Before every sweep a 1 GiB read evicts L2, so that no phase finds a
+    # matrix slice the previous sweep left there (in the solve, the SpMV and
+    # the CGS2 passes run between sweeps); only the sweeps are timed.
     gs_reps = 20
     info0 = prob.info[0]
     r_gs = prob.to_storage(torch.randn(n, dtype=torch.float64, device=dev,
                                        generator=torch.Generator(device=dev).manual_seed(1)),
                            dtype=torch.float32)
     z_gs = torch.zeros_like(r_gs)
+    flush = torch.ones(1 << 28, dtype=torch.float32, device=dev)
     for _ in range(3):
+        flush.sum()
         hpg.mg_smooth(prob.h, 0, r_gs, z_gs, 1, False)
     torch.cuda.synchronize()
-    gs_graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(gs_graph):
-        for _ in range(gs_reps):
-            hpg.mg_smooth(prob.h, 0, r_gs, z_gs, 1, False)
-    gs_graph.replay()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(gs_reps)]
+    for a, c in ev:
+        flush.sum()
+        a.record(stream)
+        hpg.mg_smooth(prob.h, 0, r_gs, z_gs, 1, False)
+        c.record(stream)
     torch.cuda.synchronize()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    gs_graph.replay()
-    g1.record(stream)
-    torch.cuda.synchronize()
-    gs_ms = g0.elapsed_time(g1)
-    del gs_graph
+    gs_ms = sum(a.elapsed_time(c) for a, c in ev)
+    del flush
     cnt = info0["colour_count"]
     gs_row_bytes = metrics.gs_row_bytes(4, 4)
     gs_phases = 15
     gs_bytes = (sum(cnt) + sum(cnt[:7])) * gs_row_bytes * gs_reps
     gs_gbs = gs_bytes / (gs_ms / 1e3) / 1e9
     traffic = gs_traffic(w.name)
+    # the same kernel inside the profiled solve (event-bracketed launches)
+    gs0 = [p for p in prof if p["name"] == "gs_colour_phase" and p["level"] == 0
+           and p["prec"] == hpg.HPG_FP32]
+    gs_in_solve = (gs0[0]["bytes"] / (gs0[0]["total_ms"] / 1e3) / 1e9) if gs0 else None
+    # whole solve: the library's algorithmic bytes of every launch of one
+    # solve (its per-launch byte model, summed by the profiler) over the
+    # graph-timed time per solve
+    solve_bytes = sum(p["bytes"] for p in prof)
+    solve_gbs = solve_bytes / (ms_max / args.steps / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "gs_phase_kernel (level 0, fp32)",
                 "achieved": gs_gbs, "peak": peak, "unit": "GB/s", "frac": gs_gbs / peak,
                 "peak_source": peak_src,
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": gs_bytes / (gs_reps * gs_phases),
+                "row_bytes": gs_row_bytes,
                 "launches": gs_reps * gs_phases,
                 "avg_launch_us": 1e3 * gs_ms / (gs_reps * gs_phases),
-                "timing": "CUDA events around a graph of %d hpg_mg_smooth sweeps on level 0 "
-                          "(%d phase launches)" % (gs_reps, gs_reps * gs_phases)}
+                "timing": "CUDA events around each of %d hpg_mg_smooth sweeps on level 0 "
+                          "(%d phase launches), L2 evicted before each" % (gs_reps,
+                                                                          gs_reps * gs_phases),
+                "in_solve": {"achieved": gs_in_solve,
+                             "frac": gs_in_solve / peak if gs_in_solve else None,
+                             "timing": "event-bracketed level-0 phases of one eager solve"},
+                "solve": {"bytes": solve_bytes, "achieved": solve_gbs,
+                          "frac": solve_gbs / peak,
+                          "timing": "sum of per-launch algorithmic bytes of one solve over "
+                                    "the graph-timed ms_per_step"}}
     kernels = [{"name": p["name"], "level": p["level"], "prec": p["prec"],
                 "launches": p["launches"], "share": p["total_ms"] / tot_ms,
                 "avg_us": 1e3 * p["total_ms"] / p["launches"],
                 "gbs": (p["bytes"] / (p["total_ms"] / 1e3) / 1e9) if p["total_ms"] > 0 else 0}
-               for p in prof[:12]]
+               for p in prof[:6]]
 
     # ---- end to end through the C ABI with pinned host buffers
     bh = b.cpu().pin_memory()
@@ -415,6 +450,15 @@ def run_gpu(args):
                "sample": "%d inner GMRES steps of %s (FP64 numpy/scipy oracle, 1 thread, "
                          "%.1f s; hierarchy build untimed)" % (r["iterations"], w.name,
                                                                  r["seconds"])}
+        # context: the same sample with every host core available to BLAS (the
+        # sparse products stay single-threaded), and the whole 16^3 FP64 solve
+        ra = oracle_sample(args.workload, args.cpu_sample_iters, threads=None)
+        r16 = oracle_sample("fp64_gmres30_16cube", 10000)
+        cpu["all_cores"] = {"value": ra["flops"] / ra["seconds"] / 1e9,
+                            "cores": os.cpu_count(), "seconds": ra["seconds"]}
+        cpu["full_solve_16cube"] = {"seconds": r16["seconds"],
+                                    "iterations": r16["iterations"],
+                                    "value": r16["flops"] / r16["seconds"] / 1e9}
 
     if rank == 0:
         line = {
@@ -430,20 +474,22 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (FP32 ELL matrix %.0f MB)" % (
                            prob.n_store() * 27 * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "time_to_solution_ms": ms_max / args.steps, "iterations": n_ir,
-            "rel_residual": infos[-1]["rel_residual"],
+            "gpu_launches": launches, "clocks": clocks,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_fl_sum / e2e_s_max / 1e9, "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
+            "kernels": kernels,
+            "validation": valid,
+            "penalized_value": gflops * valid["penalty"] if valid else None,
+            "iterations": n_ir, "rel_residual": infos[-1]["rel_residual"],
+            "roofline": roofline,
+            "time_to_solution_ms": ms_max / args.steps,
             "fp64": fp64,
             "speedup_vs_fp64": (gflops / fp64["value"]) if fp64 else None,
             "time_speedup_vs_fp64": (fp64["ms_per_solve"] / (ms_max / args.steps)) if fp64
             else None,
-            "penalized_value": gflops * valid["penalty"] if valid else None,
-            "validation": valid,
-            "roofline": roofline, "kernels": kernels,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_fl_sum / e2e_s_max / 1e9, "unit": "GFLOP/s",
-                    "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
-            "gpu_launches": launches, "clocks": clocks,
         }
+        line = rounded(line)
         print(json.dumps(line), flush=True)
     prob.close()
     if world > 1:
