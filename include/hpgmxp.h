@@ -234,6 +234,19 @@ HPG_API int hpg_gmres_ir_solve(hpg_problem_t* h, const double* b, double* x,
                                hpg_prec inner, hpg_prec basis,
                                hpg_solve_info* info, void* stream);
 
+/* Gradient of a scalar loss L(x) with respect to the per-cell diagonal scales
+ * theta of hpg_stencil_params, for x = A(theta)^{-1} b (the adjoint method;
+ * the paper has no differentiable solve -- this serves a torch.autograd
+ * wrapper of hpg_gmres_ir_solve).  Only a_ii = 26 theta_i depends on
+ * theta_i, so with lambda = A(theta)^{-T} dL/dx (a solve on the handle made
+ * with beta -> -beta: A(beta)^T = A(-beta)),
+ *   grad_i = dL/dtheta_i = -26 lambda_i x_i,  computed as (-26 lambda_i) x_i.
+ * lambda, x, grad: device, FP64, natural order, nx*ny*nz entries of h's
+ * fine grid; grad may alias neither input.  dL/db is lambda itself.
+ * HPG_ERR_INVALID for a NULL handle or pointer.  Asynchronous on `stream`. */
+HPG_API int hpg_diag_scale_gradient(hpg_problem_t* h, const double* lambda,
+                                    const double* x, double* grad, void* stream);
+
 /* ------------------------------------------------- many right-hand sides
  * The paper solves one right-hand side; these entry points solve R of them
  * (R = nrhs in {1, 2, 4, 8}) together, so that every matrix entry read from

@@ -18,6 +18,7 @@ from ._lib import (HPG_BF16, HPG_ERR_ALLOC, HPG_ERR_BREAKDOWN, HPG_ERR_CUDA,  # 
 
 __all__ = ["setup_problem", "build_mg_hierarchy", "num_levels", "level_info", "permute",
            "spmv", "mg_vcycle", "mg_smooth", "gmres_ir_solve", "destroy", "set_profiling", "set_execution",
+           "diag_scale_gradient",
            "set_option",
            "profile_report", "Problem", "HpgError",
            "HPG_FP64", "HPG_FP32", "HPG_BF16", "HPG_FP16", "load"]
@@ -142,6 +143,13 @@ def gmres_ir_solve(h, b, x, tol=1e-9, restart=30, maxit=10000, inner=HPG_FP32, b
     return d
 
 
+def diag_scale_gradient(h, lam, x, grad, stream=None):
+    """hpg_diag_scale_gradient: grad = dL/dtheta = -26 lam * x for the
+    diagonal scales of h's fine grid (FP64, natural order, n entries each)."""
+    check(load().hpg_diag_scale_gradient(h, _ptr(lam), _ptr(x), _ptr(grad), _stream(stream)),
+          "hpg_diag_scale_gradient")
+
+
 def set_profiling(h, enable=True):
     """hpg_set_profiling: per-kernel-class CUDA-event timing on/off."""
     check(load().hpg_set_profiling(h, 1 if enable else 0), "hpg_set_profiling")
@@ -162,7 +170,7 @@ def profile_report(h):
     """hpg_profile_report: list of dicts (name, level, prec, launches,
     total_ms, bytes) aggregated since profiling was enabled; clears them."""
     lib = load()
-    cap = 16 * 8 * 4   # kernel classes x levels x precisions
+    cap = 32 * 8 * 4   # kernel classes x levels x precisions
     arr = (KernelStat * cap)()
     cnt = ctypes.c_int()
     check(lib.hpg_profile_report(h, arr, cap, ctypes.byref(cnt)), "hpg_profile_report")

@@ -88,6 +88,7 @@ SIGNATURES = {
     "hpg_inject_stall": (_I, [_P, _I, _I]),
     "hpg_profile_report": (_I, [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)]),
     "hpg_destroy": (_I, [_P]),
+    "hpg_diag_scale_gradient": (_I, [_P, _P, _P, _P, _P]),
     "hpg_status_string": (ctypes.c_char_p, [_I]),
     "hpg_last_error": (ctypes.c_char_p, []),
 }

@@ -19,6 +19,7 @@ constexpr int kCoarseColour = 7;  // colour of the coarse-coincident points
 constexpr int kMaxLevels = 8;
 constexpr int kMaxRestart = 64;
 constexpr int kRowAlign = 32;     // colour blocks start on 32-row boundaries
+constexpr double kDiag = 26.0;    // diagonal of the stencil, times theta_i (Sec. 3)
 
 // ------------------------------------------------------------ error handling
 void set_error(const char* fmt, ...);
@@ -215,7 +216,7 @@ struct Profiler;    // per-kernel-class CUDA-event timing (profile.cu)
 enum KernelClass {
   K_GEN = 0, K_PERMUTE, K_SPMV, K_RESIDUAL, K_GS, K_RESTRICT, K_PROLONG, K_CGS2_GEMVT,
   K_CGS2_REORTH, K_CGS2_FINAL, K_ARNOLDI_SCALE, K_TRSM, K_COMBINE, K_UPDATE_X,
-  K_CYCLE_START, K_NORM, K_VCYCLE, K_NUM_CLASSES
+  K_CYCLE_START, K_NORM, K_VCYCLE, K_GRADIENT, K_NUM_CLASSES
 };
 const char* kernel_class_name(int cls);
 

@@ -122,7 +122,7 @@ __global__ void gen_ell_kernel(const __grid_constant__ Geom g, double beta,
     double val = 0.0;
     if (inside) {
       col = store_index(g, ni, nj, nk);
-      val = (s == kCentre) ? 26.0 * th : -1.0 + beta * (double)(dx + dy + dz) / 3.0;
+      val = (s == kCentre) ? kDiag * th : -1.0 + beta * (double)(dx + dy + dz) / 3.0;
     }
     cols[s * ns + row] = (int)col;
     v64[s * ns + row] = val;
@@ -142,6 +142,20 @@ __global__ void inject_theta_kernel(int fnx, int fny, int cnx, int cny, int cnz,
   const int J = (int)((q / cnx) % cny);
   const int K = (int)(q / ((long long)cnx * cny));
   tc[q] = tf[2LL * I + (long long)fnx * (2LL * J + (long long)fny * 2 * K)];
+}
+
+// Gradient of a loss with respect to the per-cell diagonal scales: only
+// a_ii = 26 theta_i depends on theta_i, so with x = A^{-1} b and the adjoint
+// lambda = A^{-T} dL/dx, dL/dtheta_i = -lambda_i (d a_ii / d theta_i) x_i
+// = (-26 lambda_i) x_i (natural order, FP64).
+__global__ void __launch_bounds__(256)
+diag_scale_gradient_kernel(long long n, const double* __restrict__ lam,
+                           const double* __restrict__ x, double* __restrict__ grad) {
+  pdl_trigger();
+  pdl_wait();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+    grad[i] = (-kDiag * lam[i]) * x[i];
 }
 
 template <typename Tin, typename Tout>
@@ -492,6 +506,23 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
   if (h->ws) destroy_workspace(h);   // captured graphs embed the old choice
   drop_batch_graph(h);
   return HPG_OK;
+}
+
+HPG_API int hpg_diag_scale_gradient(hpg_problem_t* h, const double* lambda, const double* x,
+                                    double* grad, void* stream) {
+  g_last_error.clear();
+  if (!h || !lambda || !x || !grad) {
+    set_error("hpg_diag_scale_gradient: invalid argument (handle or pointers)");
+    return HPG_ERR_INVALID;
+  }
+  const long long n = h->lev[0].n;
+  h->pdl_next = false;
+  const cudaStream_t s = (cudaStream_t)stream;
+  return launch(h, K_GRADIENT, 0, HPG_FP64, 24.0 * n, s, "diag_scale_gradient_kernel", [&] {
+    return kl(h, diag_scale_gradient_kernel, (int)std::min<long long>(grid_for(n, 256),
+                                                                      8LL * h->num_sms),
+              256, s, n, lambda, x, grad);
+  });
 }
 
 HPG_API int hpg_inject_stall(hpg_problem_t* h, int level, int tiles) {

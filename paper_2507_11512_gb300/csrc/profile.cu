@@ -31,7 +31,7 @@ static const char* kNames[K_NUM_CLASSES] = {
     "gen_ell",      "permute",         "spmv",        "residual_fp64", "gs_colour_phase",
     "restrict",     "prolong",         "cgs2_gemvt",  "cgs2_reorth",   "cgs2_final_givens",
     "arnoldi_scale", "trsm",           "basis_combine", "update_x",    "cycle_start",
-    "norm",         "vcycle_coarse_cluster"};
+    "norm",         "vcycle_coarse_cluster", "diag_scale_gradient"};
 
 const char* kernel_class_name(int cls) {
   return (cls >= 0 && cls < K_NUM_CLASSES) ? kNames[cls] : "unknown";

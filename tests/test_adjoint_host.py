@@ -27,19 +27,32 @@ def test_rejects_wrong_sizes_and_dtypes():
 
 
 def test_backward_is_the_adjoint_formula(monkeypatch):
-    """With the library's solve replaced by a dense solve of the same operator
-    (from the oracle, CPU), autograd through StencilSolve gives dL/db = A^{-T} g
-    and dL/dtheta_i = -26 lambda_i x_i, which central differences confirm."""
+    """With the library replaced by dense CPU stand-ins of the same operator
+    (the oracle's matrix; the gradient call as its header states it),
+    autograd through StencilSolve gives dL/db = A^{-T} g and dL/dtheta_i =
+    -26 lambda_i x_i, which central differences confirm: the wrapper solves
+    the adjoint on A(-beta) and passes lambda and x in the right order."""
     from oracle import hpg_oracle as O
     dims, beta = (3, 3, 2), 0.5
     n = 18
 
-    def dense_solve(dims_, beta_, theta, rhs, tol, restart, maxit, inner, basis, levels):
-        A = O.build_matrix(*dims_, beta_, theta.numpy()).toarray()
+    class FakeProblem:
+        def __init__(self, dims_, beta_, theta, levels):
+            self.h = (tuple(dims_), beta_, theta.clone())
+
+    def dense_solve(p, beta_, rhs, tol, restart, maxit, inner, basis):
+        dims_, b_, theta = p.h
+        assert b_ == beta_
+        A = O.build_matrix(*dims_, b_, theta.numpy()).toarray()
         x = np.linalg.solve(A, rhs.numpy())
         return torch.tensor(x, dtype=torch.float64), {"status": 0}
 
+    def gradient(h, lam, x, grad, stream=None):
+        grad.copy_((-26.0 * lam) * x)
+
+    monkeypatch.setattr(adjoint, "_problem", FakeProblem)
     monkeypatch.setattr(adjoint, "_solve", dense_solve)
+    monkeypatch.setattr(adjoint, "diag_scale_gradient", gradient)
     rng = np.random.default_rng(0)
     theta0 = torch.tensor(rng.uniform(0.9, 1.1, n))
     b0 = torch.tensor(rng.standard_normal(n))

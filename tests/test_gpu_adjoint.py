@@ -116,3 +116,32 @@ def test_96cube_forward_and_adjoint_residuals():
             ax = p.to_natural(p.spmv(p.to_storage(sol)))
         assert torch.linalg.norm(rhs - ax) <= 1e-9 * torch.linalg.norm(rhs)
     assert torch.allclose(tt.grad, -26.0 * lam * x.detach(), rtol=0, atol=0)
+
+
+def test_diag_scale_gradient_kernel_and_problem_reuse():
+    """hpg_diag_scale_gradient computes (-26 lambda_i) x_i; repeated passes
+    with the same theta reuse the cached forward and adjoint problems, and a
+    new theta builds new ones."""
+    dims = (16, 12, 8)
+    n = 16 * 12 * 8
+    theta, b, xt = inputs(dims, 15)
+    adjoint.clear_cache()
+    s0 = adjoint.cache_stats()
+    g1 = gpu_grads(dims, 0.5, theta, b, xt, tol=1e-12)
+    g2 = gpu_grads(dims, 0.5, theta, b, xt, tol=1e-12)
+    s1 = adjoint.cache_stats()
+    assert s1["builds"] - s0["builds"] == 2 and s1["reuses"] - s0["reuses"] == 2
+    for a, c in zip(g1[2:], g2[2:]):
+        np.testing.assert_array_equal(a, c)
+    gpu_grads(dims, 0.5, theta * 1.01, b, xt, tol=1e-12)
+    assert adjoint.cache_stats()["builds"] - s1["builds"] == 2
+    adjoint.clear_cache()
+    rng = np.random.default_rng(2)
+    lam = torch.tensor(rng.standard_normal(n), device=DEV)
+    x = torch.tensor(rng.standard_normal(n), device=DEV)
+    out = torch.full_like(x, float("nan"))
+    with hpg.Problem(*dims, beta=0.5, theta=theta) as p:
+        hpg.diag_scale_gradient(p.h, lam, x, out)
+        torch.testing.assert_close(out, (-26.0 * lam) * x, rtol=0, atol=0)
+        with pytest.raises(hpg.HpgError):
+            hpg.diag_scale_gradient(p.h, lam, None, out)

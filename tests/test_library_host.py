@@ -75,6 +75,7 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.hpg_inject_stall(None, 0, 1) == _lib.HPG_ERR_INVALID
     assert lib.hpg_build_mg_hierarchy(None, 4, 1, 1) == _lib.HPG_ERR_INVALID
     assert lib.hpg_destroy(None) == _lib.HPG_OK
+    assert lib.hpg_diag_scale_gradient(None, None, None, None, None) == _lib.HPG_ERR_INVALID
     cnt = ctypes.c_int()
     assert lib.hpg_profile_report(None, None, 0, ctypes.byref(cnt)) == _lib.HPG_ERR_INVALID
 
