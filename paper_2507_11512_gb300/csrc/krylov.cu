@@ -398,10 +398,20 @@ __device__ bool block_partials_last(const A (&acc)[KMAX], int nred, double* __re
   const bool mx = MAXLAST && j == nred - 1;
   double s = 0.0;
   if (j < nred) {
-#pragma unroll 4
-    for (int b = grp; b < (int)gridDim.x; b += groups) {
-      const double v = __ldcg(partials + (long long)b * kPartStride + j);
-      s = mx ? fmax(s, v) : s + v;
+    // blocks grp, grp + groups, ... in ascending order; 16 loads in flight
+    // per thread, so the serial tail is a few L2 round trips
+    constexpr int kBatch = 16;
+    const int G = (int)gridDim.x;
+    for (int b0 = grp; b0 < G; b0 += kBatch * groups) {
+      double v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int b = b0 + u * groups;
+        v[u] = b < G ? __ldcg(partials + (long long)b * kPartStride + j) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (b0 + u * groups < G) s = mx ? fmax(s, v[u]) : s + v[u];
     }
   }
   red2[threadIdx.x] = s;
@@ -420,18 +430,21 @@ __device__ bool block_partials_last(const A (&acc)[KMAX], int nred, double* __re
   return true;
 }
 
-// Arnoldi column and Givens update of Algorithm 3 for inner step k, run by
-// one warp: H[:,k] = h1 + h2, H[k+1,k] = beta; rotations 0..k-1 applied to
-// the column, rotation k formed to zero H[k+1,k], t updated, rho = |t[k+1]|.
-// The column and the rotations are staged in shared memory so the serial
-// recurrence runs on shared-memory operands.  In graph mode the next step's
-// IF node (handle `next`) is opened while the cycle stays active.
+// Arnoldi column and Givens update of Algorithm 3 for inner step k, in two
+// parts.  The column is H[:,k] = h1 + h2 with H[k+1,k] = beta.  Applying the
+// old rotations 0..k-1 to it touches rows 0..k only, so it needs h1 and h2
+// but not beta: one warp of the final CGS2 pass does it while the pass
+// streams (arnoldi_rotate_warp) and leaves the rotated column in H[0..k, k].
+// Once beta = ||w''|| is known, the last block forms rotation k that zeroes
+// H[k+1,k], updates t and rho = |t[k+1]| (arnoldi_givens_warp).  Same
+// operations in the same order as applying everything at the end.  In graph
+// mode the next step's IF node (handle `next`) is opened while the cycle
+// stays active.
 template <int KMAX>
-__device__ void arnoldi_givens_warp(double beta, int k, const double* __restrict__ h1,
+__device__ void arnoldi_rotate_warp(int k, const double* __restrict__ h1,
                                     const double* __restrict__ h2, double* __restrict__ H,
-                                    int ldh, double* __restrict__ cs, double* __restrict__ sn,
-                                    double* __restrict__ t, SolveState* st,
-                                    unsigned long long next) {
+                                    int ldh, const double* __restrict__ cs,
+                                    const double* __restrict__ sn) {
   __shared__ double hs[KMAX + 1], css[KMAX], sns[KMAX];
   const int lane = threadIdx.x & 31;
   for (int j = lane; j <= k; j += 32) {
@@ -441,46 +454,56 @@ __device__ void arnoldi_givens_warp(double beta, int k, const double* __restrict
       sns[j] = sn[j];
     }
   }
-  if (lane == 0) hs[k + 1] = beta;
   __syncwarp();
   if (lane == 0) {
-    st->beta = beta;
-    bool go = false;
-    if (!isfinite(beta)) {
-      st->status = HPG_ERR_NAN;
-      st->active = 0;
-    } else {
-      for (int j = 0; j < k; ++j) {
-        const double a = hs[j], b = hs[j + 1];
-        hs[j] = css[j] * a + sns[j] * b;
-        hs[j + 1] = -sns[j] * a + css[j] * b;
-      }
-      const double mu = hypot(hs[k], hs[k + 1]);
-      if (!(mu > 0.0) || !isfinite(mu)) {
-        st->status = isfinite(mu) ? HPG_ERR_BREAKDOWN : HPG_ERR_NAN;
-        st->active = 0;
-      } else {
-        const double c = hs[k] / mu, sv = hs[k + 1] / mu;
-        cs[k] = c;
-        sn[k] = sv;
-        hs[k] = mu;
-        hs[k + 1] = 0.0;
-        const double tk = t[k];
-        t[k + 1] = -sv * tk;
-        t[k] = c * tk;
-        const double rho = fabs(-sv * tk);
-        st->rho = rho;
-        st->k = k + 1;
-        st->iters += 1;
-        go = !(rho / st->rho0 < st->tol || st->iters >= st->maxit || k + 1 >= st->m);
-        st->active = go ? 1 : 0;
-      }
+    for (int j = 0; j < k; ++j) {
+      const double a = hs[j], b = hs[j + 1];
+      hs[j] = css[j] * a + sns[j] * b;
+      hs[j + 1] = -sns[j] * a + css[j] * b;
     }
-    if (next) cudaGraphSetConditional(next, go ? 1u : 0u);
   }
   __syncwarp();
   double* hc = H + (long long)k * ldh;
-  for (int j = lane; j <= k + 1; j += 32) hc[j] = hs[j];
+  for (int j = lane; j <= k; j += 32) hc[j] = hs[j];
+}
+
+__device__ void arnoldi_givens_warp(double beta, int k, double* __restrict__ H, int ldh,
+                                    double* __restrict__ cs, double* __restrict__ sn,
+                                    double* __restrict__ t, SolveState* st,
+                                    unsigned long long next) {
+  if ((threadIdx.x & 31) != 0) return;
+  double* hc = H + (long long)k * ldh;
+  st->beta = beta;
+  bool go = false;
+  if (!isfinite(beta)) {
+    st->status = HPG_ERR_NAN;
+    st->active = 0;
+    hc[k + 1] = beta;
+  } else {
+    const double a = __ldcg(hc + k);   // H[k,k] after the old rotations
+    const double mu = hypot(a, beta);
+    if (!(mu > 0.0) || !isfinite(mu)) {
+      st->status = isfinite(mu) ? HPG_ERR_BREAKDOWN : HPG_ERR_NAN;
+      st->active = 0;
+      hc[k + 1] = beta;
+    } else {
+      const double c = a / mu, sv = beta / mu;
+      cs[k] = c;
+      sn[k] = sv;
+      hc[k] = mu;
+      hc[k + 1] = 0.0;
+      const double tk = t[k];
+      t[k + 1] = -sv * tk;
+      t[k] = c * tk;
+      const double rho = fabs(-sv * tk);
+      st->rho = rho;
+      st->k = k + 1;
+      st->iters += 1;
+      go = !(rho / st->rho0 < st->tol || st->iters >= st->maxit || k + 1 >= st->m);
+      st->active = go ? 1 : 0;
+    }
+  }
+  if (next) cudaGraphSetConditional(next, go ? 1u : 0u);
 }
 
 // One CGS2 pass (kind KIND) over the basis columns q_0..q_{ncol-1} stored as
@@ -517,6 +540,10 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
       shc[j] = (T)(S ? hc[j] * (double)qscale[j] : hc[j]);
     __syncthreads();
   }
+  // the rotations that do not need beta, by one warp while the pass streams;
+  // block 0 takes its ticket (and the last block reads H) only afterwards
+  if (KIND == kFinal && blockIdx.x == 0 && threadIdx.x < 32)
+    arnoldi_rotate_warp<KMAX>(ncol - 1, h1, h2, H, ldh, cs, sn);
   T acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = T(0);
@@ -605,7 +632,7 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
       out[j] = S ? sums[j] * (double)qscale[j] : sums[j];
   } else if (threadIdx.x < 32) {
     if (MAXLAST && threadIdx.x == 0) st->wmax = sums[1];
-    arnoldi_givens_warp<KMAX>(sqrt(sums[0]), ncol - 1, h1, h2, H, ldh, cs, sn, t, st, next);
+    arnoldi_givens_warp(sqrt(sums[0]), ncol - 1, H, ldh, cs, sn, t, st, next);
   }
 }
 
