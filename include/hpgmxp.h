@@ -393,6 +393,12 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
 #define HPG_OPT_COARSE_CLUSTER 1
 #define HPG_OPT_PDL 2
 #define HPG_OPT_GS_PIPELINE 3
+/* HPG_OPT_GS_HALO (default 0): on levels whose matrix streams from memory,
+ * FP32 Gauss-Seidel phases that read every slot stage the part of z their
+ * rows can touch in shared memory (bulk asynchronous copies issued while the
+ * matrix loads are in flight) and gather from there; same results.  Its
+ * copy wait is bounded like the pipelined sweep's (HPG_ERR_TIMEOUT). */
+#define HPG_OPT_GS_HALO 4
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);
 
 /* Failure-detection test support (not a step of the method): the next

@@ -152,6 +152,52 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// ------------------------------------------------- TMA bulk copies, mbarriers
+// 1-D bulk copies global -> shared by the TMA engine, completion counted in
+// bytes on a shared-memory mbarrier.  Addresses must be 16-byte aligned and
+// sizes multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the given phase parity; false if the limit ran out (each
+// try_wait suspends for at most a short hardware-defined time, so the limit
+// is well under a few seconds).
+constexpr unsigned kMbarWaitLimit = 1u << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
+  for (unsigned it = 0; it < kMbarWaitLimit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
 // Slots (bit s) a Gauss-Seidel phase of colour c reads.  Normally every slot;
 // in the first forward sweep from z = 0 only the diagonal and the slots whose
 // neighbour colour is below c: colours not yet visited are still zero, so
@@ -239,6 +285,7 @@ struct hpg_problem {
   bool pdl_enabled = true;  // programmatic dependent launch on the chain
   bool pdl_next = false;    // the previous stream operation was a kernel
   bool coarse_cluster = false;    // coarse levels of a V-cycle in one cluster kernel
+  bool gs_halo = false;           // streamed GS phases stage z's neighbourhood in shared memory
   int gs_pipeline = 1;            // pipelined sweep kernel: 0 never; on streamed levels
                                   // 1 FP64 sweeps only (measured faster there), 2 always;
                                   // 3 every level

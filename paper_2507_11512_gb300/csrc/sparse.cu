@@ -10,6 +10,7 @@
 // are contiguous, so a warp reads each slot of 32 consecutive rows as one
 // 128-byte (FP32) or 256-byte (FP64) transaction.
 
+#include <limits.h>
 #include <string.h>
 
 #include <algorithm>
@@ -112,6 +113,173 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
   }
   const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
   x[row] = acc / diag;
+}
+
+// TMA-tiled variant of the streamed phase (option HPG_OPT_GS_HALO): a CTA
+// takes whole x-lines of its colour block -- lines J0 .. J0+L-1 of plane K --
+// and moves everything its rows read into shared memory with 1-D bulk
+// asynchronous copies (TMA) completing on one mbarrier: the 27 value and 26
+// index slices of its rows, their r, and the z values the rows can touch.  A
+// neighbour of a point of colour c in colour c' lies in plane K or K-1 / K+1
+// of block c' (which one follows from c's z parity, when c and c' differ in
+// z), and in lines J0-1 .. J0+L-1 or J0 .. J0+L of it (likewise in y), whole
+// lines in x: at most 11 contiguous runs of block storage per tile.  Then
+// every thread computes its row from shared memory alone; a gather reads
+// index col + delta[slot], delta being the shared-memory offset of the run
+// holding that slot's neighbours minus the run's start in the vector.  Same
+// slots, order and arithmetic as gs_phase_kernel: results equal bit for bit.
+// STREAM marks the matrix copies evict-first in L2.  The copy wait is
+// bounded: if it runs out the CTA sets `err` (the solve then reports
+// HPG_ERR_TIMEOUT), waits (bounded) once more for its copies and skips its
+// rows.
+constexpr int kHaloMaxThreads = 256;
+constexpr int kHaloRuns = 24;   // (colour, plane offset) pairs: 8 x 3
+
+template <typename T>
+__host__ __device__ constexpr int halo_align() { return 16 / (int)sizeof(T); }
+
+// Lines per CTA for a colour block with x extent cdx (whole lines, at most
+// kHaloMaxThreads rows); 0 if a line alone is longer.
+__host__ __device__ inline int halo_lines(int cdx) {
+  return cdx > kHaloMaxThreads || cdx < 1 ? 0 : kHaloMaxThreads / cdx;
+}
+// Elements of one staged row slice (the tile's rows, aligned out on both ends).
+__host__ __device__ inline int halo_rpad(int rows, int align) {
+  return (rows + 2 * align + align - 1) / align * align;
+}
+
+__device__ __forceinline__ void bulk_g2s_evict_first(void* dst, const void* src, unsigned bytes,
+                                                     unsigned long long* bar,
+                                                     unsigned long long pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
+
+template <typename T, bool STREAM>
+__global__ void __launch_bounds__(kHaloMaxThreads)
+gs_phase_halo_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
+                     const T* __restrict__ r, T* x, const __grid_constant__ Geom g, int c,
+                     int L, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char halo_smem[];
+  __shared__ unsigned long long bar;
+  __shared__ long long run_delta[kHaloRuns];
+  __shared__ int sdelta[kSlots];
+  __shared__ unsigned s_total;
+  constexpr int A = halo_align<T>();
+  const int cdx = g.cdx[c], cdy = g.cdy[c];
+  const int njt = (cdy + L - 1) / L;
+  const int K = blockIdx.x / njt;
+  const int J0 = (blockIdx.x % njt) * L;
+  const int Lr = min(L, cdy - J0);
+  const int nrows = Lr * cdx;
+  const int rpad = halo_rpad(L * cdx, A);
+  const long long row0 = g.off[c] + (long long)cdx * (J0 + (long long)cdy * K);
+  const long long row_al = row0 & ~(long long)(A - 1);
+  const int shift = (int)(row0 - row_al);
+  const unsigned slice = (unsigned)((shift + nrows + A - 1) / A * A);   // elements
+  T* sv = reinterpret_cast<T*>(halo_smem);                 // [27][rpad]
+  int* sc = reinterpret_cast<int*>(sv + kSlots * rpad);     // [27][rpad]
+  T* sr = reinterpret_cast<T*>(sc + kSlots * rpad);         // [rpad]
+  T* sx = sr + rpad;                                        // staged z runs
+  if (threadIdx.x < 32) {
+    // lane i plans z run i = (colour c2 = i / 3, plane offset dk = i % 3 - 1)
+    const int lane = threadIdx.x;
+    const int pz = colour_parity_z(c), py = colour_parity_y(c);
+    long long gs_al = 0;
+    unsigned elems = 0;
+    if (lane < kHaloRuns) {
+      const int c2 = lane / 3, dk = lane % 3 - 1;
+      const int diff = c ^ c2;
+      bool use = c2 != c;
+      if (dk != 0) use = use && (diff & 4) && (dk == -1 ? pz == 0 : pz == 1);
+      int jlo = J0, jhi = J0 + Lr - 1;
+      if (diff & 2) {
+        if (py == 0) jlo -= 1;
+        else jhi += 1;
+      }
+      jlo = max(jlo, 0);
+      jhi = min(jhi, g.cdy[c2] - 1);
+      const int kp = K + dk;
+      use = use && kp >= 0 && kp < g.cdz[c2] && jlo <= jhi;
+      if (use) {
+        const long long gs0 =
+            g.off[c2] + (long long)g.cdx[c2] * (jlo + (long long)g.cdy[c2] * kp);
+        const long long ge0 = gs0 + (long long)g.cdx[c2] * (jhi - jlo + 1);
+        gs_al = gs0 & ~(long long)(A - 1);
+        const long long ge_al = (ge0 + A - 1) & ~(long long)(A - 1);
+        elems = (unsigned)(ge_al - gs_al);
+      }
+    }
+    // exclusive prefix sum of the run sizes: shared-memory offsets
+    unsigned incl = elems;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned soff = incl - elems;
+    const unsigned zt = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane < kHaloRuns)
+      run_delta[lane] = elems ? (long long)soff - gs_al : (long long)(-(1LL << 40));
+    if (lane == 0) {
+      mbar_init(&bar, 1);
+      fence_mbar_init();
+      // 27 value slices, 26 index slices (not the centre's), r, the z runs
+      mbar_expect_tx(&bar, (unsigned)sizeof(T) * (kSlots * slice + slice + zt) +
+                               4u * (kSlots - 1) * slice);
+      s_total = zt;
+    }
+    __syncwarp();
+    unsigned long long pol = 0;
+    if (STREAM)
+      asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    if (elems) bulk_g2s(sx + soff, x + gs_al, elems * (unsigned)sizeof(T), &bar);
+    if (lane < kSlots) {
+      const T* vsrc = vals + lane * ns + row_al;
+      if (STREAM)
+        bulk_g2s_evict_first(sv + lane * rpad, vsrc, slice * (unsigned)sizeof(T), &bar, pol);
+      else
+        bulk_g2s(sv + lane * rpad, vsrc, slice * (unsigned)sizeof(T), &bar);
+      if (lane != kCentre) {
+        const int* csrc = cols + lane * ns + row_al;
+        if (STREAM)
+          bulk_g2s_evict_first(sc + lane * rpad, csrc, slice * 4u, &bar, pol);
+        else
+          bulk_g2s(sc + lane * rpad, csrc, slice * 4u, &bar);
+      }
+    }
+    if (lane == kSlots) bulk_g2s(sr, r + row_al, slice * (unsigned)sizeof(T), &bar);
+    __syncwarp();
+    if (lane < kSlots && lane != kCentre) {
+      const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+      const int c2 = c ^ ((dx & 1) | ((dy & 1) << 1) | ((dz & 1) << 2));
+      const int dk = (pz + dz) >> 1;   // floor: -1, 0 or +1
+      const long long d = run_delta[c2 * 3 + dk + 1];
+      sdelta[lane] = (d < -(1LL << 31) || d > (1LL << 31)) ? INT_MIN / 2 : (int)d;
+    }
+  }
+  __syncthreads();
+  if (!mbar_wait(&bar, 0)) {
+    if (threadIdx.x == 0 && err) atomicExch(err, 2u);
+    mbar_wait(&bar, 0);   // bounded: the copies target this CTA's shared memory
+    return;
+  }
+  const int t = threadIdx.x;
+  if (t >= nrows) return;
+  const unsigned nsm = s_total;
+  const int e = shift + t;
+  T acc = sr[e];
+#pragma unroll
+  for (int q = 0; q < kSlots; ++q) {
+    if (q == kCentre) continue;
+    const unsigned idx = (unsigned)(sc[q * rpad + e] + sdelta[q]);
+    const T xv = idx < nsm ? sx[idx] : T(0);
+    acc = fma(-sv[q * rpad + e], xv, acc);
+  }
+  x[row0 + t] = acc / sv[kCentre * rpad + e];
 }
 
 // The bandwidth-variant instantiation of a phase of colour c.
@@ -490,6 +658,56 @@ struct SweepState {
   int last = -1;
 };
 
+// Dynamic shared memory of a TMA-tiled phase of colour c with L lines per
+// CTA: the row slices (27 values, 27 index slots, r) and every z run the tile
+// may copy, each rounded out to 16-byte boundaries.
+template <typename T>
+static size_t halo_smem_bytes(const Geom& g, int c, int L) {
+  const size_t rpad = (size_t)halo_rpad(L * g.cdx[c], halo_align<T>());
+  size_t bytes = rpad * (kSlots * sizeof(T) + kSlots * 4 + sizeof(T));
+  size_t elems = 0;
+  for (int c2 = 0; c2 < kColours; ++c2) {
+    if (c2 == c) continue;
+    const int diff = c ^ c2;
+    const int planes = (diff & 4) ? 2 : 1;
+    const int lines = L + ((diff & 2) ? 1 : 0);
+    elems += (size_t)planes * ((size_t)lines * g.cdx[c2] + 2 * halo_align<T>());
+  }
+  return bytes + elems * sizeof(T);
+}
+
+// Launches the TMA-tiled phase when it applies (option set, FP32, whole lines
+// fit a CTA, r and z 16-byte aligned); returns false to use gs_phase_kernel.
+template <typename T, bool STREAM>
+static bool launch_gs_halo(hpg_problem* h, const Level& L, const T* r, T* z, int c,
+                           cudaStream_t s, cudaError_t* e) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+  if (!h->gs_halo || (((uintptr_t)z | (uintptr_t)r) & 15u) != 0) return false;
+  const int lines = halo_lines(L.g.cdx[c]);
+  if (lines < 1 || L.cnt[c] == 0) return false;
+  const size_t smem = halo_smem_bytes<T>(L.g, c, lines);
+  if (smem > (160u << 10)) return false;
+  if (smem > (48u << 10) &&
+      cudaFuncSetAttribute(gs_phase_halo_kernel<T, STREAM>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int threads = (lines * L.g.cdx[c] + 31) / 32 * 32;
+  const int grid = L.g.cdz[c] * ((L.g.cdy[c] + lines - 1) / lines);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  *e = cudaLaunchKernelEx(&cfg, gs_phase_halo_kernel<T, STREAM>, Prec<T>::vals(L),
+                          (const int*)L.cols, L.g.n_store, r, z, L.g, c, lines, h->pipe_err);
+  return true;
+  }
+}
+
 template <typename T>
 static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool from_zero,
                     SweepState& st, cudaStream_t s, bool keep = false) {
@@ -508,6 +726,11 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                 "gs_phase_kernel", [&] {
                   if (L.g.n_store * 27LL * 8 > kStreamMatrixBytes) {
                     h->pdl_next = false;   // full serialisation (see gs_phase_kernel)
+                    cudaError_t he = cudaSuccess;
+                    if (!from_zero &&
+                        (keep ? launch_gs_halo<T, false>(h, L, r, z, c, s, &he)
+                              : launch_gs_halo<T, true>(h, L, r, z, c, s, &he)))
+                      return he;
                     if (keep)   // slice read again soon after: leave it in L2
                       return kl(h, gs_phase_fn<T, false>(c, from_zero),
                                 grid_for(nrows, kThreads), kThreads, s, vals, L.cols,

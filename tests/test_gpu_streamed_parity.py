@@ -157,3 +157,41 @@ def test_streamed_mxp_solve_80cube_matches_oracle(basis):
 def test_streamed_mxp_solve_128cube_matches_oracle():
     """The benchmark grid and solver settings, to 1e-12 against the oracle."""
     solve_vs_oracle((128, 128, 128), hpg.HPG_FP32)
+
+
+@pytest.mark.parametrize("dims", GRIDS)
+def test_halo_staged_phases_equal_plain_phases(dims):
+    """HPG_OPT_GS_HALO: the streamed FP32 phases that stage z in shared memory
+    give the plain phases' results bit for bit (smoother, V-cycle)."""
+    with hpg.Problem(*dims, beta=BETA, levels=4) as p:
+        for l in range(p.levels):
+            info = p.info[l]
+            r = random_vector(info["n"], seed=91 + l, dtype=np.float32)
+            z0 = random_vector(info["n"], seed=92 + l, dtype=np.float32)
+            rt = torch.tensor(to_storage(r, info["dims"]), device=DEV)
+            out = []
+            for opt in (0, 1):
+                hpg.set_option(p.h, hpg.HPG_OPT_GS_HALO, opt)
+                zt = torch.tensor(to_storage(z0, info["dims"]), device=DEV)
+                hpg.mg_smooth(p.h, l, rt, zt, 2, False)
+                out.append((zt, p.vcycle(rt, level=l)))
+            hpg.set_option(p.h, hpg.HPG_OPT_GS_HALO, 0)
+            torch.testing.assert_close(out[0][0], out[1][0], rtol=0, atol=0)
+            torch.testing.assert_close(out[0][1], out[1][1], rtol=0, atol=0)
+
+
+def test_halo_staged_solve_equals_plain_solve():
+    dims = (80, 80, 80)
+    n = 80 ** 3
+    b = torch.tensor(random_vector(n, seed=5), device=DEV)
+    with hpg.Problem(*dims, beta=BETA) as p:
+        xs, its = [], []
+        for opt in (0, 1):
+            hpg.set_option(p.h, hpg.HPG_OPT_GS_HALO, opt)
+            x = torch.zeros_like(b)
+            info = hpg.gmres_ir_solve(p.h, b, x, tol=1e-10, inner=hpg.HPG_FP32)
+            assert info["status"] == 0
+            xs.append(x)
+            its.append(info["iterations"])
+    assert its[0] == its[1]
+    torch.testing.assert_close(xs[0], xs[1], rtol=0, atol=0)
