@@ -399,6 +399,18 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
  * matrix loads are in flight) and gather from there; same results.  Its
  * copy wait is bounded like the pipelined sweep's (HPG_ERR_TIMEOUT). */
 #define HPG_OPT_GS_HALO 4
+/* HPG_OPT_COARSE_CTA (default 0): the coarsest level's symmetric sweep of a
+ * V-cycle runs in one CTA (z in shared memory, a block barrier between colour
+ * phases) when every colour block has at most 512 rows and the level's vector
+ * fits in 64 KB; 0: one launch per colour phase there too.  Same results.
+ * Ignored while HPG_OPT_GS_PIPELINE is 3.
+ * HPG_OPT_PDL_ROWS (default 16384): Gauss-Seidel phases of levels whose
+ * matrix does not stream from memory are launched with programmatic
+ * dependent launch (their matrix loads overlap the previous phase) up to
+ * this many rows per phase; larger phases wait for the previous one to end.
+ * Same results. */
+#define HPG_OPT_COARSE_CTA 5
+#define HPG_OPT_PDL_ROWS 6
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);
 
 /* Failure-detection test support (not a step of the method): the next

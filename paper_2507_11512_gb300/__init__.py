@@ -13,7 +13,8 @@ from ._lib import (HPG_BF16, HPG_ERR_ALLOC, HPG_ERR_BREAKDOWN, HPG_ERR_CUDA,  # 
                    HPG_ERR_INVALID, HPG_ERR_NAN, HPG_ERR_NOT_CONVERGED, HPG_ERR_STATE,
                    HPG_ERR_TIMEOUT, HPG_ERR_UNSUPPORTED, HPG_EXEC_EAGER, HPG_EXEC_GRAPH,
                    HPG_FP16, HPG_FP32,
-                   HPG_FP64, HPG_OK, HPG_OPT_COARSE_CLUSTER, HPG_OPT_GS_HALO, HPG_OPT_GS_PIPELINE,
+                   HPG_FP64, HPG_OK, HPG_OPT_COARSE_CLUSTER, HPG_OPT_COARSE_CTA, HPG_OPT_GS_HALO,
+                   HPG_OPT_GS_PIPELINE, HPG_OPT_PDL_ROWS,
                    HPG_OPT_PDL, HpgError,
                    KernelStat, LevelDesc, SolveInfo, StencilParams, check, load)
 

@@ -24,6 +24,7 @@ HPG_ERR_TIMEOUT = -9
 HPG_FP64, HPG_FP32, HPG_BF16, HPG_FP16 = 0, 1, 2, 3
 HPG_EXEC_GRAPH, HPG_EXEC_EAGER = 0, 1
 HPG_OPT_COARSE_CLUSTER, HPG_OPT_PDL, HPG_OPT_GS_PIPELINE, HPG_OPT_GS_HALO = 1, 2, 3, 4
+HPG_OPT_COARSE_CTA, HPG_OPT_PDL_ROWS = 5, 6
 
 
 class StencilParams(ctypes.Structure):

@@ -286,6 +286,9 @@ struct hpg_problem {
   bool pdl_next = false;    // the previous stream operation was a kernel
   bool coarse_cluster = false;    // coarse levels of a V-cycle in one cluster kernel
   bool gs_halo = false;           // streamed GS phases stage z's neighbourhood in shared memory
+  bool coarse_cta = false;        // coarsest level's sweep in one CTA when it fits
+  long long pdl_rows = 16384;     // latency-variant GS phases launched programmatically up
+                                  // to this many rows
   int gs_pipeline = 1;            // pipelined sweep kernel: 0 never; on streamed levels
                                   // 1 FP64 sweeps only (measured faster there), 2 always;
                                   // 3 every level

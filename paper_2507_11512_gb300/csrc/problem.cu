@@ -493,6 +493,14 @@ HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value) {
     case HPG_OPT_COARSE_CLUSTER: h->coarse_cluster = value != 0; break;
     case HPG_OPT_PDL: h->pdl_enabled = value != 0; break;
     case HPG_OPT_GS_HALO: h->gs_halo = value != 0; break;
+    case HPG_OPT_COARSE_CTA: h->coarse_cta = value != 0; break;
+    case HPG_OPT_PDL_ROWS:
+      if (value < 0) {
+        set_error("hpg_set_option: HPG_OPT_PDL_ROWS takes a row count >= 0, not %d", value);
+        return HPG_ERR_INVALID;
+      }
+      h->pdl_rows = value;
+      break;
     case HPG_OPT_GS_PIPELINE:
       if (value < 0 || value > 3) {
         set_error("hpg_set_option: HPG_OPT_GS_PIPELINE takes 0..3, not %d", value);

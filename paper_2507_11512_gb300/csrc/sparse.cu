@@ -591,7 +591,6 @@ prolong_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
 
 // ----------------------------------------------------------------- launchers
 constexpr int kThreads = 256;
-constexpr long long kPdlSmallRows = 16384;   // latency-variant phases overlapped up to this
 
 // Largest colour slice (values + indices) a streamed level's phase leaves in
 // L2 for a later phase (symgs).
@@ -743,7 +742,7 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                   // phases and slows phases of tens of thousands of rows (with
                   // the 32768-row level-1 phases overlapped too, the 128^3
                   // solve took 110.3 ms instead of 107.4)
-                  if (nrows > kPdlSmallRows) h->pdl_next = false;
+                  if (nrows > h->pdl_rows) h->pdl_next = false;
                   return kl(h, gs_small_fn<T>(mat_mode(L), c, from_zero),
                             grid_for(nrows, small_threads<T>()), small_threads<T>(), s, vals,
                             L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
@@ -842,6 +841,150 @@ static int symgs(hpg_problem* h, int level, const T* r, T* z, bool from_zero, Sw
   return HPG_OK;
 }
 
+// ------------------------------------------- coarsest level in one CTA
+// The coarsest level's symmetric sweep from z = 0 (Fig. 1: one sweep there)
+// in a single CTA, when every colour block has at most kCtaSweepRows rows:
+// z lives in shared memory, a __syncthreads() separates the colour phases
+// (instead of a kernel boundary, ~1.3 us each when launched), and each
+// thread loads the next phase's matrix row and r_i into registers while the
+// current phase computes, so the L2 latency of the matrix is off the chain.
+// Phases, slot sets, summation order and division are those of the launched
+// phases (gs_phase_small_kernel), so z is equal bit for bit.
+constexpr int kCtaSweepRows = 512;
+struct CtaSweepPhase {
+  int row0, nrows, valid_end;
+  unsigned mask;
+};
+struct CtaSweepPlan {
+  int nphases;
+  int c0_rows;   // rows [0, c0_rows) of z already hold colour 0's first phase
+  CtaSweepPhase ph[kMaxPipePhases];
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kCtaSweepRows, 1)
+coarse_sweep_cta_kernel(const T* __restrict__ vals, const int* __restrict__ cols, int ns,
+                        const T* __restrict__ r, T* __restrict__ z,
+                        const __grid_constant__ CtaSweepPlan plan) {
+  extern __shared__ __align__(16) unsigned char cta_smem[];
+  T* sz = reinterpret_cast<T*>(cta_smem);
+  const int t = threadIdx.x;
+  pdl_trigger();
+  int col[kSlots];
+  T a[kSlots];
+  T rr = T(0);
+  // phase p's row of this thread: matrix and r (no earlier kernel writes
+  // the matrix, so phase 0's loads go out before the programmatic wait)
+  auto load = [&](int p, bool rhs) {
+    const CtaSweepPhase& ph = plan.ph[p];
+    const bool live = t < ph.nrows;
+    const int row = ph.row0 + (live ? t : 0);
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) {
+      const bool use = live && ((ph.mask >> q) & 1u);
+      col[q] = use ? ld_mat<MODE>(cols + (long long)q * ns + row) : 0;
+      a[q] = use ? ld_mat<MODE>(vals + (long long)q * ns + row) : T(1);
+    }
+    if (rhs) rr = live ? r[row] : T(0);
+  };
+  load(0, false);
+  pdl_wait();
+  if (t < plan.ph[0].nrows) rr = r[plan.ph[0].row0 + t];
+  for (int i = t; i < ns; i += blockDim.x) sz[i] = i < plan.c0_rows ? z[i] : T(0);
+  __syncthreads();
+  for (int p = 0; p < plan.nphases; ++p) {
+    const CtaSweepPhase& ph = plan.ph[p];
+    T acc = rr;
+    T diag = a[kCentre];
+    const bool live = t < ph.nrows;
+    T xv[kSlots];
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q)
+      xv[q] = (q != kCentre && ((ph.mask >> q) & 1u) && col[q] < ph.valid_end) ? sz[col[q]]
+                                                                                : T(0);
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q)
+      if (q != kCentre && ((ph.mask >> q) & 1u)) acc = fma(-a[q], xv[q], acc);
+    if (p + 1 < plan.nphases) load(p + 1, true);
+    if (live) sz[ph.row0 + t] = acc / diag;
+    __syncthreads();
+  }
+  for (int i = t; i < ns; i += blockDim.x) z[i] = sz[i];
+}
+
+// Runs the coarsest level's sweep from zero in one CTA if it fits; returns
+// HPG_ERR_UNSUPPORTED otherwise (the caller launches the phases).
+template <typename T>
+static int coarsest_sweep_cta(hpg_problem* h, int level, const T* r, T* z, bool c0_done,
+                              cudaStream_t s) {
+  const Level& L = h->lev[level];
+  if (!h->coarse_cta || h->gs_pipeline == 3 ||
+      L.g.n_store * (long long)sizeof(T) > (64LL << 10))
+    return HPG_ERR_UNSUPPORTED;
+  for (int c = 0; c < kColours; ++c)
+    if (L.g.off[c + 1] - L.g.off[c] > kCtaSweepRows) return HPG_ERR_UNSUPPORTED;
+  CtaSweepPlan plan;
+  memset(&plan, 0, sizeof(plan));
+  plan.c0_rows = c0_done ? (int)L.g.off[1] : 0;
+  int last = c0_done ? 0 : -1;
+  double bytes = 0.0;
+  auto add = [&](int c, bool fz) {
+    if (last == c) return;
+    last = c;
+    const int nrows = (int)(L.g.off[c + 1] - L.g.off[c]);
+    if (nrows == 0) return;
+    CtaSweepPhase& ph = plan.ph[plan.nphases++];
+    ph.row0 = (int)L.g.off[c];
+    ph.nrows = nrows;
+    ph.valid_end = fz ? (int)L.g.off[c] : (int)L.g.n_store;
+    ph.mask = gs_slot_mask(c, fz);
+    const int nslots = __builtin_popcount(ph.mask) - 1;
+    bytes += L.cnt[c] * ((nslots + 1.0) * sizeof(T) + nslots * 4.0 +
+                         (2.0 + nslots / 26.0) * sizeof(T));
+  };
+  for (int c = 0; c < kColours; ++c) add(c, true);
+  for (int c = kColours - 1; c >= 0; --c) add(c, false);
+  if (plan.nphases == 0) return HPG_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(T) * (size_t)L.g.n_store;
+  const int mode = mat_mode(L);
+  auto kern = mode == kMatResident ? coarse_sweep_cta_kernel<T, kMatResident>
+                                   : coarse_sweep_cta_kernel<T, kMatCached>;
+  if (smem > (48u << 10) &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return HPG_ERR_UNSUPPORTED;
+  }
+  return launch(h, K_GS, level, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32, bytes, s,
+                "coarse_sweep_cta_kernel", [&] {
+                  cudaLaunchConfig_t cfg = {};
+                  cfg.gridDim = dim3(1u);
+                  cfg.blockDim = dim3((unsigned)kCtaSweepRows);
+                  cfg.dynamicSmemBytes = smem;
+                  cfg.stream = s;
+                  cudaLaunchAttribute attr[1];
+                  if (h->pdl_enabled && h->pdl_next && !h->profiling) {
+                    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    attr[0].val.programmaticStreamSerializationAllowed = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                  }
+                  return cudaLaunchKernelEx(&cfg, kern, Prec<T>::vals(L), (const int*)L.cols,
+                                            (int)L.g.n_store, r, z, plan);
+                });
+}
+
+// The coarsest level of a V-cycle: one symmetric sweep from z = 0.
+template <typename T>
+static int coarsest_sweep(hpg_problem* h, int l, const T* r, T* z, bool c0_done,
+                          cudaStream_t s) {
+  int rc = coarsest_sweep_cta<T>(h, l, r, z, c0_done, s);
+  if (rc != HPG_ERR_UNSUPPORTED) return rc;
+  SweepState st;
+  if (c0_done) st.last = 0;
+  return symgs<T>(h, l, r, z, true, st, s);
+}
+
 // Whether the restriction from level l also runs the first phase (colour 0)
 // of level l+1's first sweep from zero: true when that sweep goes through the
 // launched phases (not the cluster kernel) and starts from zero (the
@@ -858,7 +1001,7 @@ static int vcycle_t(hpg_problem* h, int l, const T* r, T* z, cudaStream_t s,
   if (c0_done) st.last = 0;   // colour 0 of the first sweep came with the restriction
   int rc = launch_vcycle_cluster(h, l, Prec<T>::idx == 0 ? HPG_FP64 : HPG_FP32, r, z, s);
   if (rc != HPG_ERR_UNSUPPORTED) return rc;   // small level: the rest runs in one cluster
-  if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
+  if (l == h->nlev - 1) return coarsest_sweep<T>(h, l, r, z, c0_done, s);
   if (h->pre == 0) {
     HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
     h->pdl_next = false;
@@ -1022,7 +1165,7 @@ static int vcycle_noalloc_t(hpg_problem* h, int l, const T* r, T* z, T* const* c
   SweepState st;
   if (c0_done) st.last = 0;   // colour 0 of the first sweep came with the restriction
   int rc;
-  if (l == h->nlev - 1) return symgs<T>(h, l, r, z, true, st, s);
+  if (l == h->nlev - 1) return coarsest_sweep<T>(h, l, r, z, c0_done, s);
   if (h->pre == 0) {
     HPG_CK(cudaMemsetAsync(z, 0, sizeof(T) * L.g.n_store, s));
     h->pdl_next = false;

@@ -378,3 +378,45 @@ def test_solve_same_with_and_without_cluster_vcycle(inner):
     np.testing.assert_array_equal(x2.cpu().numpy(), x3.cpu().numpy())
     r = np.linalg.norm(b - lv[0].A @ x1.cpu().numpy()) / np.linalg.norm(b)
     assert r < 1e-9
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16), (24, 20, 28), (40, 36, 28), (64, 64, 64),
+                                  (96, 96, 96), (128, 128, 128), (12, 12, 12), (2, 2, 2)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_coarsest_sweep_in_one_cta_equals_phase_launches(dims, dtype):
+    # HPG_OPT_COARSE_CTA: the coarsest level's sweep in one CTA (z in shared
+    # memory) against one launch per colour phase: same phases, same order;
+    # HPG_OPT_PDL_ROWS: programmatic launches of larger phases change nothing
+    with hpg.Problem(*dims, beta=0.5) as p:
+        for l in range(p.levels):
+            info = p.info[l]
+            r = random_vector(info["n"], seed=17 + l,
+                              dtype=np.float64 if dtype == torch.float64 else np.float32)
+            rt = torch.tensor(to_storage(r, info["dims"]), dtype=dtype, device=DEV)
+            hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CTA, 1)
+            z1 = p.vcycle(rt, l)
+            hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CTA, 0)
+            z2 = p.vcycle(rt, l)
+            torch.testing.assert_close(z1, z2, rtol=0, atol=0)
+            hpg.set_option(p.h, hpg.HPG_OPT_PDL_ROWS, 1 << 30)
+            z3 = p.vcycle(rt, l)
+            hpg.set_option(p.h, hpg.HPG_OPT_PDL_ROWS, 16384)
+            torch.testing.assert_close(z1, z3, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("inner", [hpg.HPG_FP32, hpg.HPG_FP64])
+def test_solve_same_with_and_without_coarsest_cta(inner):
+    dims, beta = (64, 64, 64), 0.5
+    lv = oracle_hierarchy(dims, 4, beta)
+    b = lv[0].A @ x_true(lv[0].n) + rhs_noise(lv[0].n, 1e-3)
+    with hpg.Problem(*dims, beta=beta) as p:
+        bt = gpu(b, torch.float64)
+        xs = []
+        for opt in (1, 0):
+            hpg.set_option(p.h, hpg.HPG_OPT_COARSE_CTA, opt)
+            hpg.set_option(p.h, hpg.HPG_OPT_PDL_ROWS, (1 << 30) if opt else 16384)
+            x = torch.zeros_like(bt)
+            info = hpg.gmres_ir_solve(p.h, bt, x, inner=inner)
+            assert info["status"] == 0
+            xs.append(x)
+    torch.testing.assert_close(xs[0], xs[1], rtol=0, atol=0)
