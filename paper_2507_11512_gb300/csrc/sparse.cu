@@ -115,6 +115,25 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
   x[row] = acc / diag;
 }
 
+// The bandwidth-variant instantiation of a phase of colour c.
+template <typename T, bool STREAM>
+using GsPhaseFn = void (*)(const T*, const int*, long long, const T*, T*, long long, long long,
+                           long long);
+template <typename T, bool STREAM>
+static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
+  if (!from_zero) return gs_phase_kernel<T, STREAM, -1>;
+  switch (c) {
+    case 0: return gs_phase_kernel<T, STREAM, 0>;
+    case 1: return gs_phase_kernel<T, STREAM, 1>;
+    case 2: return gs_phase_kernel<T, STREAM, 2>;
+    case 3: return gs_phase_kernel<T, STREAM, 3>;
+    case 4: return gs_phase_kernel<T, STREAM, 4>;
+    case 5: return gs_phase_kernel<T, STREAM, 5>;
+    case 6: return gs_phase_kernel<T, STREAM, 6>;
+    default: return gs_phase_kernel<T, STREAM, 7>;
+  }
+}
+
 // TMA-tiled variant of the streamed phase (option HPG_OPT_GS_HALO): a CTA
 // takes whole x-lines of its colour block -- lines J0 .. J0+L-1 of plane K --
 // and moves everything its rows read into shared memory with 1-D bulk
@@ -280,25 +299,6 @@ gs_phase_halo_kernel(const T* __restrict__ vals, const int* __restrict__ cols, l
     acc = fma(-sv[q * rpad + e], xv, acc);
   }
   x[row0 + t] = acc / sv[kCentre * rpad + e];
-}
-
-// The bandwidth-variant instantiation of a phase of colour c.
-template <typename T, bool STREAM>
-using GsPhaseFn = void (*)(const T*, const int*, long long, const T*, T*, long long, long long,
-                           long long);
-template <typename T, bool STREAM>
-static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
-  if (!from_zero) return gs_phase_kernel<T, STREAM, -1>;
-  switch (c) {
-    case 0: return gs_phase_kernel<T, STREAM, 0>;
-    case 1: return gs_phase_kernel<T, STREAM, 1>;
-    case 2: return gs_phase_kernel<T, STREAM, 2>;
-    case 3: return gs_phase_kernel<T, STREAM, 3>;
-    case 4: return gs_phase_kernel<T, STREAM, 4>;
-    case 5: return gs_phase_kernel<T, STREAM, 5>;
-    case 6: return gs_phase_kernel<T, STREAM, 6>;
-    default: return gs_phase_kernel<T, STREAM, 7>;
-  }
 }
 
 // Threads per CTA of the latency variant; measured on GB300 at 128^3, the
