@@ -189,6 +189,26 @@ def main(argv=None):
                                                                       i["restarts"], 30))
     its = [i["iterations"] for inf in infos for i in inf]
     ok = all(i["converged"] for inf in infos for i in inf)
+    # byte-model roofline: the library's algorithmic bytes of every launch of
+    # each system's batched solve (profiled one system at a time, from x0 = 0;
+    # same iterations as in the batch) over the batch solve's time
+    from . import profile_report, set_profiling
+    total_bytes = 0.0
+    for pr, b in zip(probs, Bs):
+        x = torch.zeros_like(b)
+        set_profiling(pr.h, True)
+        solve_batch(pr.h, b, x, tol=a.tol)
+        total_bytes += sum(r["bytes"] for r in profile_report(pr.h))
+        set_profiling(pr.h, False)
+    peak = None
+    import json as _json
+    import os as _os
+    pk = _os.path.join(_os.path.dirname(_os.path.dirname(_os.path.abspath(__file__))),
+                       "MEASURED_PEAKS.json")
+    if _os.path.exists(pk):
+        with open(pk) as f:
+            peak = _json.load(f).get("hbm_gbs")
+    gbs = total_bytes / (ms / 1e3) / 1e9
     unknowns = sum(s["dims"][0] * s["dims"][1] * s["dims"][2] for s in spec)
     print(json.dumps({
         "workload": "batch_%dsys_%drhs" % (a.systems, a.nrhs), "systems": a.systems,
@@ -197,7 +217,11 @@ def main(argv=None):
         "rhs_solved_per_s": a.systems * a.nrhs / (ms / 1e3),
         "iterations_min_median_max": [min(its), sorted(its)[len(its) // 2], max(its)],
         "setup_s": setup_s, "tune_and_capture_s": create_s, "tuned": not a.no_tune,
-        "lanes_per_row": shape[0], "tuning_solve_ms_by_lanes_per_row": tune_ms}))
+        "lanes_per_row": shape[0], "tuning_solve_ms_by_lanes_per_row": tune_ms,
+        "roofline": {"bound": "hbm", "bytes": total_bytes, "achieved": gbs, "unit": "GB/s",
+                     "peak": peak, "frac": gbs / peak if peak else None,
+                     "timing": "library per-launch algorithmic bytes of every system's "
+                               "batched solve over the batch solve's CUDA-event time"}}))
     solver.close()
     for p in probs:
         p.close()

@@ -107,15 +107,22 @@ mspmv_kernel(const float* __restrict__ vals, const int* __restrict__ cols, long 
 
 // One Gauss-Seidel colour phase (Sec. 3.2.1) for R right-hand sides: rows
 // [row0, row0 + nrows) of one colour block; entries j >= valid_end read as
-// zero (first forward sweep from z = 0); MASKED: slots outside `mask` are
-// known zero and not loaded.  Same slot order and arithmetic per value as
-// gs_phase_kernel.
-template <int R, int LPR, bool STREAM, bool MASKED>
+// zero (first forward sweep from z = 0).  MC selects the slots loaded:
+// kAllSlots every slot; c = 0..7 the first forward sweep's phase of colour c
+// from z = 0 with its slot set (gs_slot_mask) fixed at compile time, so a
+// row's loads issue as one straight-line batch; kMaskSlots the same set
+// passed at run time in `mask` (the other slots are known zero and not
+// loaded).  MODE (MatLoad) is the level's matrix load policy: streamed
+// evict-first, cached, or evict-last for the small coarse levels.  Same slot
+// order and arithmetic per value as gs_phase_kernel.
+constexpr int kAllSlots = -1, kMaskSlots = -2;
+template <int R, int LPR, int MODE, int MC>
 __global__ void __launch_bounds__(256)
 mgs_phase_kernel(const float* __restrict__ vals, const int* __restrict__ cols, long long ns,
                  const float* __restrict__ rhs, float* z, long long row0, long long nrows,
                  long long valid_end, unsigned mask) {
   constexpr int RL = R / LPR;
+  constexpr unsigned kMask = MC >= 0 ? gs_slot_mask(MC, true) : (1u << kSlots) - 1u;
   pdl_trigger();
   pdl_wait();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -127,13 +134,13 @@ mgs_phase_kernel(const float* __restrict__ vals, const int* __restrict__ cols, l
   ld_n<RL>(rhs + row * R + lane * RL, acc);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
-    if (s == kCentre) continue;
-    const bool use = !MASKED || ((mask >> s) & 1u);
+    if (s == kCentre || !((kMask >> s) & 1u)) continue;
+    const bool use = MC != kMaskSlots || ((mask >> s) & 1u);
     float a = 0.0f;
     int c = 0;
     if (use) {
-      a = ld_matrix<STREAM>(vals + s * ns + row);
-      c = ld_matrix<STREAM>(cols + s * ns + row);
+      a = ld_mat<MODE>(vals + s * ns + row);
+      c = ld_mat<MODE>(cols + s * ns + row);
     }
     float xv[RL];
     if (use && c < valid_end) {
@@ -145,14 +152,15 @@ mgs_phase_kernel(const float* __restrict__ vals, const int* __restrict__ cols, l
 #pragma unroll
     for (int r = 0; r < RL; ++r) acc[r] = fma(-a, xv[r], acc[r]);
   }
-  const float diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
+  const float diag = ld_mat<MODE>(vals + kCentre * ns + row);
 #pragma unroll
   for (int r = 0; r < RL; ++r) acc[r] = acc[r] / diag;
   st_n<RL>(z + row * R + lane * RL, acc);
 }
 
-// Fused residual + injection restriction (Sec. 3.2.4) for R right-hand sides.
-template <int R, bool STREAM>
+// Fused residual + injection restriction (Sec. 3.2.4) for R right-hand sides;
+// MODE as for mgs_phase_kernel.
+template <int R, int MODE>
 __global__ void __launch_bounds__(256)
 mrestrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                  const float* __restrict__ vals, const int* __restrict__ cols,
@@ -170,8 +178,8 @@ mrestrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom g
   ld_n<R>(rhs + row * R, acc);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
-    const float a = ld_matrix<STREAM>(vals + s * ns + row);
-    const int c = ld_matrix<STREAM>(cols + s * ns + row);
+    const float a = ld_mat<MODE>(vals + s * ns + row);
+    const int c = ld_mat<MODE>(cols + s * ns + row);
     float xv[R];
     ldg_n<R>(z + (long long)c * R, xv);
 #pragma unroll
@@ -359,40 +367,86 @@ static Shape shape_of(hpg_problem* h, int level, int kind, int R) {
   return sh;
 }
 
-template <int R, int LPR>
-static cudaError_t mgs_launch(hpg_problem* h, bool stream, bool masked, int grid, int block,
+// Load policy of a level's matrix (as in sparse.cu): streamed evict-first
+// where the FP32 ELL arrays exceed the streaming size, evict-last where they
+// are small (coarse levels read by every V-cycle), cached otherwise.
+static int mmat_mode(const Level& L) {
+  const long long b = L.g.n_store * 27LL * 8;
+  return b > kStreamMatrixBytes ? kMatStream : b > kResidentMatrixBytes ? kMatCached
+                                                                        : kMatResident;
+}
+
+template <int R, int LPR, int MODE, int MC>
+static cudaError_t mgs_kl(hpg_problem* h, int grid, int block, cudaStream_t s, const float* vals,
+                          const int* cols, long long ns, const float* rhs, float* z,
+                          long long row0, long long nrows, long long valid_end, unsigned mask) {
+  return kl(h, mgs_phase_kernel<R, LPR, MODE, MC>, grid, block, s, vals, cols, ns, rhs, z, row0,
+            nrows, valid_end, mask);
+}
+
+// Colour c of the first sweep from zero with its compile-time slot set.
+template <int R, int MODE>
+static cudaError_t mgs_colour(hpg_problem* h, int c, int grid, int block, cudaStream_t s,
+                              const float* vals, const int* cols, long long ns,
+                              const float* rhs, float* z, long long row0, long long nrows,
+                              long long valid_end, unsigned mask) {
+  switch (c) {
+#define HPG_MGS_CASE(C)                                                                   \
+  case C:                                                                                 \
+    return mgs_kl<R, 1, MODE, C>(h, grid, block, s, vals, cols, ns, rhs, z, row0, nrows, \
+                                 valid_end, mask);
+    HPG_MGS_CASE(0) HPG_MGS_CASE(1) HPG_MGS_CASE(2) HPG_MGS_CASE(3)
+    HPG_MGS_CASE(4) HPG_MGS_CASE(5) HPG_MGS_CASE(6) HPG_MGS_CASE(7)
+#undef HPG_MGS_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int R, int LPR, int MODE>
+static cudaError_t mgs_launch(hpg_problem* h, int c, bool masked, int grid, int block,
                               cudaStream_t s, const float* vals, const int* cols, long long ns,
                               const float* rhs, float* z, long long row0, long long nrows,
                               long long valid_end, unsigned mask) {
-  if (stream) {
-    if (masked)
-      return kl(h, mgs_phase_kernel<R, LPR, true, true>, grid, block, s, vals, cols, ns, rhs, z,
-                row0, nrows, valid_end, mask);
-    return kl(h, mgs_phase_kernel<R, LPR, true, false>, grid, block, s, vals, cols, ns, rhs, z,
-              row0, nrows, valid_end, mask);
-  }
-  if (masked)
-    return kl(h, mgs_phase_kernel<R, LPR, false, true>, grid, block, s, vals, cols, ns, rhs, z,
-              row0, nrows, valid_end, mask);
-  return kl(h, mgs_phase_kernel<R, LPR, false, false>, grid, block, s, vals, cols, ns, rhs, z,
-            row0, nrows, valid_end, mask);
+  if (!masked)
+    return mgs_kl<R, LPR, MODE, kAllSlots>(h, grid, block, s, vals, cols, ns, rhs, z, row0,
+                                           nrows, valid_end, mask);
+  if constexpr (LPR == 1)
+    return mgs_colour<R, MODE>(h, c, grid, block, s, vals, cols, ns, rhs, z, row0, nrows,
+                               valid_end, mask);
+  return mgs_kl<R, LPR, MODE, kMaskSlots>(h, grid, block, s, vals, cols, ns, rhs, z, row0, nrows,
+                                          valid_end, mask);
+}
+
+template <int R, int LPR>
+static cudaError_t mgs_mode(hpg_problem* h, int mode, int c, bool masked, int grid, int block,
+                            cudaStream_t s, const float* vals, const int* cols, long long ns,
+                            const float* rhs, float* z, long long row0, long long nrows,
+                            long long valid_end, unsigned mask) {
+  if (mode == kMatStream)
+    return mgs_launch<R, LPR, kMatStream>(h, c, masked, grid, block, s, vals, cols, ns, rhs, z,
+                                          row0, nrows, valid_end, mask);
+  if (mode == kMatResident)
+    return mgs_launch<R, LPR, kMatResident>(h, c, masked, grid, block, s, vals, cols, ns, rhs,
+                                            z, row0, nrows, valid_end, mask);
+  return mgs_launch<R, LPR, kMatCached>(h, c, masked, grid, block, s, vals, cols, ns, rhs, z,
+                                        row0, nrows, valid_end, mask);
 }
 
 template <int R>
-static cudaError_t mgs_dispatch(hpg_problem* h, int lpr, bool stream, bool masked, long long nrows,
-                                int block, cudaStream_t s, const float* vals, const int* cols,
-                                long long ns, const float* rhs, float* z, long long row0,
-                                long long valid_end, unsigned mask) {
+static cudaError_t mgs_dispatch(hpg_problem* h, int lpr, int mode, int c, bool masked,
+                                long long nrows, int block, cudaStream_t s, const float* vals,
+                                const int* cols, long long ns, const float* rhs, float* z,
+                                long long row0, long long valid_end, unsigned mask) {
   constexpr int L2 = R >= 2 ? 2 : 1;
   const int grid = grid_for(nrows * lpr, block);
   if (lpr == 1)
-    return mgs_launch<R, 1>(h, stream, masked, grid, block, s, vals, cols, ns, rhs, z, row0,
-                            nrows, valid_end, mask);
+    return mgs_mode<R, 1>(h, mode, c, masked, grid, block, s, vals, cols, ns, rhs, z, row0,
+                          nrows, valid_end, mask);
   if (lpr == 2)
-    return mgs_launch<R, L2>(h, stream, masked, grid, block, s, vals, cols, ns, rhs, z, row0,
-                             nrows, valid_end, mask);
-  return mgs_launch<R, R>(h, stream, masked, grid, block, s, vals, cols, ns, rhs, z, row0, nrows,
-                          valid_end, mask);
+    return mgs_mode<R, L2>(h, mode, c, masked, grid, block, s, vals, cols, ns, rhs, z, row0,
+                           nrows, valid_end, mask);
+  return mgs_mode<R, R>(h, mode, c, masked, grid, block, s, vals, cols, ns, rhs, z, row0, nrows,
+                        valid_end, mask);
 }
 
 struct BSweep {
@@ -416,8 +470,8 @@ static int mgs_phase(hpg_problem* h, int level, const float* rhs, float* z, int 
   const bool stream = streamed(L);
   return launch(h, K_GS, level, HPG_FP32, L.cnt[c] * row_bytes, s, "mgs_phase_kernel", [&] {
     if (stream || nrows > kBatchPdlRows) h->pdl_next = false;
-    return mgs_dispatch<R>(h, sh.lpr, stream, from_zero, nrows, sh.block, s, L.v32, L.cols,
-                           L.g.n_store, rhs, z, row0, valid_end, mask);
+    return mgs_dispatch<R>(h, sh.lpr, mmat_mode(L), c, from_zero, nrows, sh.block, s, L.v32,
+                           L.cols, L.g.n_store, rhs, z, row0, valid_end, mask);
   });
 }
 
@@ -475,11 +529,12 @@ static int mvcycle_t(hpg_problem* h, int l, const float* rhs, float* z, cudaStre
                         L.g.cdz[kCoarseColour];
   rc = launch(h, K_RESTRICT, l, HPG_FP32, cnt * (27.0 * 8 + 3.0 * 4 * R), s, "mrestrict_kernel",
               [&] {
-                if (streamed(L))
-                  return kl(h, mrestrict_kernel<R, true>, grid_for(cnt, 256), 256, s, L.g, C.g,
-                            L.v32, L.cols, rhs, z, rcv);
-                return kl(h, mrestrict_kernel<R, false>, grid_for(cnt, 256), 256, s, L.g, C.g,
-                          L.v32, L.cols, rhs, z, rcv);
+                const int mode = mmat_mode(L);
+                auto kern = mode == kMatStream     ? mrestrict_kernel<R, kMatStream>
+                            : mode == kMatResident ? mrestrict_kernel<R, kMatResident>
+                                                   : mrestrict_kernel<R, kMatCached>;
+                return kl(h, kern, grid_for(cnt, 256), 256, s, L.g, C.g, L.v32, L.cols, rhs, z,
+                          rcv);
               });
   if (rc) return rc;
   if ((rc = mvcycle_t<R>(h, l + 1, rcv, zcv, s))) return rc;

@@ -201,3 +201,46 @@ def test_problem_outlives_its_batch():
     finally:
         pa.close()
         pb.close()
+
+
+@pytest.mark.parametrize("R", [2, 8])
+def test_streamed_size_system_columns_equal_single_vector_kernels(R):
+    """A 96^3 system (the batched workload's largest edge): its level-0 matrix
+    streams from memory, level 1 is cached, levels 2-3 are read evict-last;
+    every launch shape's columns equal the single-vector kernels bitwise."""
+    dims = (96, 96, 96)
+    with hpg.Problem(*dims, beta=0.6) as p:
+        assert p.n_store(0) * 27 * 8 > (96 << 20)
+        for level in (0, 1):
+            _, X = rvec(p, level, R, 30 + level)
+            ref_s = [p.spmv(X[:, r].contiguous(), level=level) for r in range(R)]
+            ref_v = [p.vcycle(X[:, r].contiguous(), level=level) for r in range(R)]
+            for lpr, blk in shapes(R):
+                for kind in (batch.KIND_SPMV, batch.KIND_GS):
+                    batch.set_shape(p.h, level, kind, R, lpr, blk)
+                Y = torch.empty_like(X)
+                batch.spmv_batch(p.h, level, X, Y)
+                Z = torch.empty_like(X)
+                batch.vcycle_batch(p.h, level, X, Z)
+                for r in range(R):
+                    assert torch.equal(Y[:, r], ref_s[r]), (level, lpr, blk, r)
+                    assert torch.equal(Z[:, r], ref_v[r]), (level, lpr, blk, r)
+            for kind in (batch.KIND_SPMV, batch.KIND_GS):
+                batch.set_shape(p.h, level, kind, R, 0, 0)
+
+
+def test_streamed_size_batched_solve_matches_oracle():
+    dims, beta = (96, 96, 96), 0.6
+    lv = oracle_hierarchy(dims, 4, beta)
+    n = lv[0].n
+    rhs = [lv[0].A @ x_true(n) + rhs_noise(n, 1e-3, seed=3), rhs_noise(n, 1.0, seed=4)]
+    B = torch.tensor(np.stack(rhs), device=DEV)
+    X = torch.zeros_like(B)
+    with hpg.Problem(*dims, beta=beta) as p:
+        infos = batch.solve_batch(p.h, B, X, tol=1e-12)
+    x = X.cpu().numpy()
+    for r in range(2):
+        assert infos[r]["converged"] == 1 and infos[r]["status"] == 0, (r, infos[r])
+        assert np.linalg.norm(rhs[r] - lv[0].A @ x[r]) / np.linalg.norm(rhs[r]) < 1e-12
+        x_o, _ = O.gmres_ir(lv, rhs[r], tol=1e-12, restart=30)
+        assert np.linalg.norm(x[r] - x_o) / np.linalg.norm(x_o) <= 1e-8
