@@ -405,10 +405,10 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
  * fits in 64 KB; 0: one launch per colour phase there too.  Same results.
  * Ignored while HPG_OPT_GS_PIPELINE is 3.
  * HPG_OPT_PDL_ROWS (default 16384): Gauss-Seidel phases of levels whose
- * matrix does not stream from memory are launched with programmatic
- * dependent launch (their matrix loads overlap the previous phase) up to
- * this many rows per phase; larger phases wait for the previous one to end.
- * Same results. */
+ * matrix does not stream from memory, up to this many rows per phase, let
+ * the next kernel launch as soon as they start (their own matrix loads then
+ * overlap the previous phase); larger phases let it launch only as their
+ * blocks exit.  Same results. */
 #define HPG_OPT_COARSE_CTA 5
 #define HPG_OPT_PDL_ROWS 6
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);

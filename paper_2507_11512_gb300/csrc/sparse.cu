@@ -317,6 +317,10 @@ __host__ __device__ constexpr int small_threads() {
 // programmatic wait -- the matrix does not depend on earlier kernels -- so that
 // latency overlaps the previous phase; after the wait it issues all the
 // gathers of x at once.  Same slot order and arithmetic as gs_phase_kernel.
+// early != 0: the next kernel may launch as soon as this one starts (the
+// small phases of levels 2-3; without it the 128^3 solve took 145.8 instead
+// of 102.9 ms); 0: only as this one's blocks exit (the 32768-row level-1
+// phases: 102.9 -> 102.3 ms, while an early trigger there made it 105.6 ms).
 // MODE (MatLoad): kMatCached, or kMatResident for the small levels whose
 // matrix is kept in L2 evict-last.  MC as in gs_phase_kernel: -1 all slots,
 // c the first forward sweep's colour c (slots with a later neighbour colour
@@ -325,9 +329,9 @@ template <typename T, int MODE, int MC>
 __global__ void __launch_bounds__(small_threads<T>())
 gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                       const T* __restrict__ r, T* x, long long row0, long long nrows,
-                      long long valid_end) {
+                      long long valid_end, int early) {
   constexpr unsigned kMask = MC < 0 ? (1u << kSlots) - 1u : gs_slot_mask(MC, true);
-  pdl_trigger();
+  if (early) pdl_trigger();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool live = t < nrows;
   const long long row = row0 + (live ? t : 0);
@@ -356,7 +360,7 @@ gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, 
 // The latency-variant instantiation of a phase of colour c.
 template <typename T>
 using GsSmallFn = void (*)(const T*, const int*, long long, const T*, T*, long long, long long,
-                           long long);
+                           long long, int);
 template <typename T, int MODE>
 static GsSmallFn<T> gs_small_fn_mode(int c, bool from_zero) {
   if (!from_zero) return gs_phase_small_kernel<T, MODE, -1>;
@@ -749,10 +753,10 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                   // phases and slows phases of tens of thousands of rows (with
                   // the 32768-row level-1 phases overlapped too, the 128^3
                   // solve took 110.3 ms instead of 107.4)
-                  if (nrows > h->pdl_rows) h->pdl_next = false;
+                  const int early = nrows > h->pdl_rows ? 0 : 1;
                   return kl(h, gs_small_fn<T>(mat_mode(L), c, from_zero),
                             grid_for(nrows, small_threads<T>()), small_threads<T>(), s, vals,
-                            L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                            L.cols, L.g.n_store, r, z, row0, nrows, valid_end, early);
                 });
 }
 
