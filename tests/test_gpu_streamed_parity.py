@@ -195,3 +195,40 @@ def test_halo_staged_solve_equals_plain_solve():
             its.append(info["iterations"])
     assert its[0] == its[1]
     torch.testing.assert_close(xs[0], xs[1], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_streamed_vcycle_symmetric_theta_scaled(dtype):
+    """beta = 0 (the paper's benchmarked symmetric matrix) with a per-cell
+    diagonal scale theta ~ U(0.9, 1.1) at a streamed size: the V-cycle from
+    every level against the oracle's (theta injected on the coarse levels)."""
+    dims = (80, 80, 80)
+    theta = np.random.default_rng(21).uniform(0.9, 1.1, 80 ** 3)
+    lv = O.build_hierarchy(*dims, levels=4, beta=0.0, theta=theta)
+    with hpg.Problem(*dims, beta=0.0, theta=theta) as p:
+        assert streamed(p.info[0])
+        for l, L in enumerate(lv):
+            r = random_vector(L.n, seed=101 + l, dtype=npdtype(dtype)).astype(np.float64)
+            rt = torch.tensor(to_storage(r, L.dims), dtype=dtype, device=DEV)
+            z = to_natural(p.vcycle(rt, level=l).cpu().numpy(), L.dims).astype(np.float64)
+            assert close(z, O.vcycle(lv, r, l), dtype), l
+
+
+def test_streamed_fp64_gmres_matches_oracle():
+    """Plain FP64 GMRES(30) (Algorithm 2) at a streamed size: its sweeps on the
+    streamed level run as the pipelined kernel; x against the oracle's at 1e-8
+    and the iteration counts within a few steps."""
+    dims = (80, 80, 80)
+    lv = oracle_hierarchy(dims, 4, BETA)
+    n = lv[0].n
+    b = lv[0].A @ x_true(n) + rhs_noise(n, 1e-3, seed=2)
+    x_o, info_o = O.gmres_ir(lv, b, tol=1e-12, restart=30)
+    with hpg.Problem(*dims, beta=BETA) as p:
+        bt = torch.tensor(b, device=DEV)
+        xt = torch.zeros_like(bt)
+        info = hpg.gmres_ir_solve(p.h, bt, xt, tol=1e-12, restart=30, inner=hpg.HPG_FP64)
+        x = xt.cpu().numpy()
+    assert info["status"] == 0
+    assert np.linalg.norm(b - lv[0].A @ x) / np.linalg.norm(b) < 1e-12
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= 1e-8
+    assert abs(info["iterations"] - info_o.iterations) <= 3
