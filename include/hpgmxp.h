@@ -394,16 +394,19 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
 #define HPG_OPT_PDL 2
 #define HPG_OPT_GS_PIPELINE 3
 /* HPG_OPT_GS_HALO (default 0): on levels whose matrix streams from memory,
- * FP32 Gauss-Seidel phases that read every slot stage the part of z their
- * rows can touch in shared memory (bulk asynchronous copies issued while the
- * matrix loads are in flight) and gather from there; same results.  Its
- * copy wait is bounded like the pipelined sweep's (HPG_ERR_TIMEOUT). */
+ * FP32 Gauss-Seidel phases that read every slot run TMA-tiled: a CTA moves
+ * its rows' 27 value and 26 index slices, their r and the part of z its rows
+ * can touch into shared memory with bulk asynchronous copies completing on
+ * one mbarrier, then computes from shared memory; same results (measured
+ * slower than the default on GB300).  Its copy wait is bounded: if it runs
+ * out the solve returns HPG_ERR_TIMEOUT. */
 #define HPG_OPT_GS_HALO 4
 /* HPG_OPT_COARSE_CTA (default 0): the coarsest level's symmetric sweep of a
  * V-cycle runs in one CTA (z in shared memory, a block barrier between colour
  * phases) when every colour block has at most 512 rows and the level's vector
- * fits in 64 KB; 0: one launch per colour phase there too.  Same results.
- * Ignored while HPG_OPT_GS_PIPELINE is 3.
+ * fits in 64 KB; 0: one launch per colour phase there too.  Same results
+ * (measured slower than the default on GB300).  Ignored while
+ * HPG_OPT_GS_PIPELINE is 3.
  * HPG_OPT_PDL_ROWS (default 16384): Gauss-Seidel phases of levels whose
  * matrix does not stream from memory, up to this many rows per phase, let
  * the next kernel launch as soon as they start (their own matrix loads then
