@@ -232,3 +232,22 @@ def test_streamed_fp64_gmres_matches_oracle():
     assert np.linalg.norm(b - lv[0].A @ x) / np.linalg.norm(b) < 1e-12
     assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= 1e-8
     assert abs(info["iterations"] - info_o.iterations) <= 3
+
+
+@pytest.mark.parametrize("pre,post", [(0, 2), (2, 1), (1, 3)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_streamed_vcycle_sweep_counts(pre, post, dtype):
+    """Other pre/post sweep counts at a streamed size: pre = 0 starts from a
+    zeroed z with no first phase fused into the restriction; more sweeps
+    repeat the full phases."""
+    dims = (80, 80, 80)
+    lv = oracle_hierarchy(dims, 4, BETA)
+    with hpg.Problem(*dims, beta=BETA, levels=4, pre_sweeps=pre, post_sweeps=post) as p:
+        r = random_vector(lv[0].n, seed=111, dtype=npdtype(dtype)).astype(np.float64)
+        rt = torch.tensor(to_storage(r, lv[0].dims), dtype=dtype, device=DEV)
+        z = to_natural(p.vcycle(rt).cpu().numpy(), lv[0].dims).astype(np.float64)
+    assert close(z, O.vcycle(lv, r, 0, pre, post), dtype)
+
+
+def test_streamed_mxp_solve_fp16_basis_matches_oracle():
+    solve_vs_oracle((80, 80, 80), hpg.HPG_FP16)
