@@ -706,6 +706,13 @@ __device__ bool bgivens_warp(double beta, int k, const double* __restrict__ h1,
 }
 
 enum BPassKind { kBGemvT = 0, kBReorth = 1, kBFinal = 2 };
+
+// Rows per thread per iteration of the multi-right-hand-side CGS2 passes: the
+// KMAX x V basis values of an iteration take at most 64 registers.
+template <int KMAX>
+__host__ __device__ constexpr int mpass_vec() {
+  return KMAX <= 16 ? 4 : KMAX <= 32 ? 2 : 1;
+}
 constexpr int kHStride = kMaxRestart + 1;   // per-RHS stride of h1, h2, cs, sn, t, y
 
 // One CGS2 pass (Algorithm 3, CGS2 procedure) for R right-hand sides, each
@@ -722,7 +729,9 @@ mcgs2_pass_kernel(const float* __restrict__ Q, long long len, int ncol, float* w
                   double* __restrict__ out, double* __restrict__ H, int ldh,
                   double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ t,
                   BState* st, int* runs, unsigned long long next) {
-  __shared__ float shc[R][KMAX];
+  // one row of coefficients per right-hand side; rows padded by one so that
+  // the R rows a warp reads at once (r = lane % R) fall into distinct banks
+  __shared__ float shc[R][KMAX + 1];
   __shared__ double sums[KMAX * R];
   __shared__ double hs[R][kMaxRestart + 2], css[R][kMaxRestart], sns[R][kMaxRestart];
   pdl_trigger();
@@ -737,30 +746,56 @@ mcgs2_pass_kernel(const float* __restrict__ Q, long long len, int ncol, float* w
   float acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = 0.0f;
-  const long long stride = (long long)gridDim.x * kBThreads;
-  for (long long e = blockIdx.x * (long long)kBThreads + threadIdx.x; e < len; e += stride) {
-    float wr = __ldcs(w + e);
-    float q[KMAX];
+  // A thread keeps one right-hand side r (the block size and the grid stride
+  // are multiples of R) and takes V consecutive storage rows of it per
+  // iteration, issuing all their basis and w loads before any arithmetic, so
+  // that KMAX x V loads are in flight (in the in-place passes the store to
+  // wout could otherwise hold back the next row's loads).  Row group g holds
+  // rows g*V .. g*V+V-1; their elements sit R apart, and the R lanes of a row
+  // together read R contiguous values.
+  constexpr int V = mpass_vec<KMAX>();
+  const long long rows = len / R;
+  const long long ng = rows / V;
+  const long long slot0 = (blockIdx.x * (long long)kBThreads + threadIdx.x) / R;
+  const long long nslots = (long long)gridDim.x * (kBThreads / R);
+  for (long long g = slot0; g < ng; g += nslots) {
+    const long long e0 = g * V * R + r;
+    float wr[V];
+    float q[KMAX][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) wr[v] = __ldcs(w + e0 + v * R);
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-      if (j < ncol) q[j] = __ldcs(Q + j * len + e);
+      if (j < ncol) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) q[j][v] = __ldcs(Q + j * len + e0 + v * R);
+      }
     if (KIND == kBGemvT) {
 #pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < ncol) acc[j] = fma(q[j], wr, acc[j]);
-    } else {
-      float sc = 0.0f;
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < ncol) sc = fma(q[j], shc[r][j], sc);
-      wr = wr - sc;
-      wout[e] = wr;
-      if (KIND == kBReorth) {
+      for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int j = 0; j < KMAX; ++j)
-          if (j < ncol) acc[j] = fma(q[j], wr, acc[j]);
-      } else {
-        acc[0] = fma(wr, wr, acc[0]);
+          if (j < ncol) acc[j] = fma(q[j][v], wr[v], acc[j]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        float sc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+          if (j < ncol) sc = fma(q[j][v], shc[r][j], sc);
+        wr[v] = wr[v] - sc;
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) wout[e0 + v * R] = wr[v];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (KIND == kBReorth) {
+#pragma unroll
+          for (int j = 0; j < KMAX; ++j)
+            if (j < ncol) acc[j] = fma(q[j][v], wr[v], acc[j]);
+        } else {
+          acc[0] = fma(wr[v], wr[v], acc[0]);
+        }
       }
     }
   }
