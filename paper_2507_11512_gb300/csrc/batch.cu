@@ -117,44 +117,49 @@ mspmv_kernel(const float* __restrict__ vals, const int* __restrict__ cols, long 
 // order and arithmetic per value as gs_phase_kernel.
 constexpr int kAllSlots = -1, kMaskSlots = -2;
 template <int R, int LPR, int MODE, int MC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 mgs_phase_kernel(const float* __restrict__ vals, const int* __restrict__ cols, long long ns,
                  const float* __restrict__ rhs, float* z, long long row0, long long nrows,
                  long long valid_end, unsigned mask) {
   constexpr int RL = R / LPR;
   constexpr unsigned kMask = MC >= 0 ? gs_slot_mask(MC, true) : (1u << kSlots) - 1u;
   pdl_trigger();
-  pdl_wait();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long lr = t / LPR;
   const int lane = (int)(t % LPR);
   if (lr >= nrows) return;
   const long long row = row0 + lr;
+  // the row's matrix slots first, all at once (the matrix does not depend on
+  // earlier kernels, so these loads may overlap the previous phase), then the
+  // gathers slot by slot; the arithmetic is that of gs_phase_kernel
+  int col[kSlots];
+  float a[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const bool use = ((kMask >> s) & 1u) && (MC != kMaskSlots || s == kCentre ||
+                                             ((mask >> s) & 1u));
+    col[s] = use && s != kCentre ? ld_mat<MODE>(cols + s * ns + row) : 0;
+    a[s] = use ? ld_mat<MODE>(vals + s * ns + row) : 0.0f;
+  }
+  pdl_wait();
   float acc[RL];
   ld_n<RL>(rhs + row * R + lane * RL, acc);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     if (s == kCentre || !((kMask >> s) & 1u)) continue;
     const bool use = MC != kMaskSlots || ((mask >> s) & 1u);
-    float a = 0.0f;
-    int c = 0;
-    if (use) {
-      a = ld_mat<MODE>(vals + s * ns + row);
-      c = ld_mat<MODE>(cols + s * ns + row);
-    }
     float xv[RL];
-    if (use && c < valid_end) {
-      ldg_n<RL>(z + (long long)c * R + lane * RL, xv);
+    if (use && col[s] < valid_end) {
+      ldg_n<RL>(z + (long long)col[s] * R + lane * RL, xv);
     } else {
 #pragma unroll
       for (int r = 0; r < RL; ++r) xv[r] = 0.0f;
     }
 #pragma unroll
-    for (int r = 0; r < RL; ++r) acc[r] = fma(-a, xv[r], acc[r]);
+    for (int r = 0; r < RL; ++r) acc[r] = fma(-a[s], xv[r], acc[r]);
   }
-  const float diag = ld_mat<MODE>(vals + kCentre * ns + row);
 #pragma unroll
-  for (int r = 0; r < RL; ++r) acc[r] = acc[r] / diag;
+  for (int r = 0; r < RL; ++r) acc[r] = acc[r] / a[kCentre];
   st_n<RL>(z + row * R + lane * RL, acc);
 }
 
@@ -648,13 +653,16 @@ __device__ bool mblock_partials_last(const A (&acc)[KMAX], int ncol, double* par
 }
 
 // Arnoldi column and Givens update (Algorithm 3) of one right-hand side, one
-// warp; as in the single solve.  Returns whether this right-hand side's cycle
-// continues.
-__device__ bool bgivens_warp(double beta, int k, const double* __restrict__ h1,
-                             const double* __restrict__ h2, double* __restrict__ H, int ldh,
-                             double* __restrict__ cs, double* __restrict__ sn,
-                             double* __restrict__ t, BState* st, double* hs, double* css,
-                             double* sns) {
+// warp, in two parts as in the single solve: brotate_warp applies the old
+// rotations 0..k-1 to column k = h1 + h2 (rows 0..k; it needs no beta) while
+// the final pass streams, and leaves the rotated column in H; bgivens_warp,
+// once beta is known, forms rotation k from H[k,k] and beta, updates t and rho
+// and returns whether this right-hand side's cycle continues.  Same
+// operations in the same order as doing it all at the end.
+__device__ void brotate_warp(int k, const double* __restrict__ h1,
+                             const double* __restrict__ h2, double* __restrict__ hcol,
+                             const double* __restrict__ cs, const double* __restrict__ sn,
+                             double* hs, double* css, double* sns) {
   const int lane = threadIdx.x & 31;
   for (int j = lane; j <= k; j += 32) {
     hs[j] = h1[j] + h2[j];
@@ -663,30 +671,42 @@ __device__ bool bgivens_warp(double beta, int k, const double* __restrict__ h1,
       sns[j] = sn[j];
     }
   }
-  if (lane == 0) hs[k + 1] = beta;
   __syncwarp();
+  if (lane == 0) {
+    for (int j = 0; j < k; ++j) {
+      const double a = hs[j], b = hs[j + 1];
+      hs[j] = css[j] * a + sns[j] * b;
+      hs[j + 1] = -sns[j] * a + css[j] * b;
+    }
+  }
+  __syncwarp();
+  for (int j = lane; j <= k; j += 32) hcol[j] = hs[j];
+}
+
+__device__ bool bgivens_warp(double beta, int k, double* __restrict__ hcol,
+                             double* __restrict__ cs, double* __restrict__ sn,
+                             double* __restrict__ t, BState* st) {
+  const int lane = threadIdx.x & 31;
   bool go = false;
   if (lane == 0) {
     st->beta = beta;
     if (!isfinite(beta)) {
       st->status = HPG_ERR_NAN;
       st->active = 0;
+      hcol[k + 1] = beta;
     } else {
-      for (int j = 0; j < k; ++j) {
-        const double a = hs[j], b = hs[j + 1];
-        hs[j] = css[j] * a + sns[j] * b;
-        hs[j + 1] = -sns[j] * a + css[j] * b;
-      }
-      const double mu = hypot(hs[k], hs[k + 1]);
+      const double a = __ldcg(hcol + k);   // H[k,k] after the old rotations
+      const double mu = hypot(a, beta);
       if (!(mu > 0.0) || !isfinite(mu)) {
         st->status = isfinite(mu) ? HPG_ERR_BREAKDOWN : HPG_ERR_NAN;
         st->active = 0;
+        hcol[k + 1] = beta;
       } else {
-        const double c = hs[k] / mu, sv = hs[k + 1] / mu;
+        const double c = a / mu, sv = beta / mu;
         cs[k] = c;
         sn[k] = sv;
-        hs[k] = mu;
-        hs[k + 1] = 0.0;
+        hcol[k] = mu;
+        hcol[k + 1] = 0.0;
         const double tk = t[k];
         t[k + 1] = -sv * tk;
         t[k] = c * tk;
@@ -699,9 +719,6 @@ __device__ bool bgivens_warp(double beta, int k, const double* __restrict__ h1,
       }
     }
   }
-  __syncwarp();
-  double* hc = H + (long long)k * ldh;
-  for (int j = lane; j <= k + 1; j += 32) hc[j] = hs[j];
   return __shfl_sync(0xffffffffu, go, 0);
 }
 
@@ -742,6 +759,16 @@ mcgs2_pass_kernel(const float* __restrict__ Q, long long len, int ncol, float* w
     for (int i = threadIdx.x; i < ncol * R; i += kBThreads)
       shc[i % R][i / R] = (float)hc[(i % R) * kHStride + i / R];
     __syncthreads();
+  }
+  // the old rotations of each active right-hand side's Arnoldi column, one
+  // warp per right-hand side of block 0, while the other blocks stream; block
+  // 0 takes its ticket (and the final block reads H) only afterwards
+  if (KIND == kBFinal && blockIdx.x == 0) {
+    for (int rr = threadIdx.x >> 5; rr < R; rr += kBWarps)
+      if (st[rr].active)
+        brotate_warp(ncol - 1, h1 + rr * kHStride, h2 + rr * kHStride,
+                     H + (long long)rr * ldh * (ldh - 1) + (long long)(ncol - 1) * ldh,
+                     cs + rr * kHStride, sn + rr * kHStride, hs[rr], css[rr], sns[rr]);
   }
   float acc[KMAX];
 #pragma unroll
@@ -812,10 +839,10 @@ mcgs2_pass_kernel(const float* __restrict__ Q, long long len, int ncol, float* w
   __syncthreads();
   for (int rr = warp; rr < R; rr += kBWarps) {
     if (!st[rr].active) continue;
-    const bool go = bgivens_warp(sqrt(sums[rr]), ncol - 1, h1 + rr * kHStride,
-                                 h2 + rr * kHStride, H + (long long)rr * ldh * (ldh - 1), ldh,
-                                 cs + rr * kHStride, sn + rr * kHStride, t + rr * kHStride,
-                                 st + rr, hs[rr], css[rr], sns[rr]);
+    const bool go = bgivens_warp(
+        sqrt(sums[rr]), ncol - 1,
+        H + (long long)rr * ldh * (ldh - 1) + (long long)(ncol - 1) * ldh,
+        cs + rr * kHStride, sn + rr * kHStride, t + rr * kHStride, st + rr);
     if (go && (threadIdx.x & 31) == 0) any_go = 1;
   }
   __syncthreads();
