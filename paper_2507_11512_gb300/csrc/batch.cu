@@ -781,6 +781,14 @@ mcgs2_pass_kernel(const float* __restrict__ Q, long long len, int ncol, float* w
   // rows g*V .. g*V+V-1; their elements sit R apart, and the R lanes of a row
   // together read R contiguous values.
   constexpr int V = mpass_vec<KMAX>();
+  // this thread's coefficients in registers where they fit beside the basis
+  // values and the sums (the final pass keeps one sum, up to 16 columns all)
+  constexpr bool kRegCoef = KIND == kBFinal || KMAX <= 16;
+  float coef[kRegCoef ? KMAX : 1];
+  if constexpr (kRegCoef) {
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) coef[j] = (KIND != kBGemvT && j < ncol) ? shc[r][j] : 0.0f;
+  }
   const long long rows = len / R;
   const long long ng = rows / V;
   const long long slot0 = (blockIdx.x * (long long)kBThreads + threadIdx.x) / R;
@@ -809,7 +817,7 @@ mcgs2_pass_kernel(const float* __restrict__ Q, long long len, int ncol, float* w
         float sc = 0.0f;
 #pragma unroll
         for (int j = 0; j < KMAX; ++j)
-          if (j < ncol) sc = fma(q[j][v], shc[r][j], sc);
+          if (j < ncol) sc = fma(q[j][v], kRegCoef ? coef[j] : shc[r][j], sc);
         wr[v] = wr[v] - sc;
       }
 #pragma unroll
@@ -1140,12 +1148,30 @@ static int ensure_bworkspace(hpg_problem* h, int R, int m) {
 static double* gpart_of(BatchSpace* bs) { return bs->partials + (size_t)kBatchPartStride * bs->G; }
 
 // ------------------------------------------------------ host: solve pieces
+// Grid of a multi-right-hand-side CGS2 pass: one wave of the instantiation's
+// resident blocks, at most the G blocks the partials are sized for.
+template <int R, int KMAX, int KIND>
+static int mpass_grid(hpg_problem* h) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mcgs2_pass_kernel<R, KMAX, KIND>,
+                                                      kBThreads, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  const int g = per_sm * h->num_sms;
+  return g < h->batch->G ? g : h->batch->G;
+}
+
 template <int R, int KMAX, int KIND>
 static cudaError_t enqueue_mpass(hpg_problem* h, int ncol, float* wout, double* out,
                                  unsigned long long next, cudaStream_t s) {
   BatchSpace* bs = h->batch;
   const long long len = bs->ns * R;
-  return kl(h, mcgs2_pass_kernel<R, KMAX, KIND>, bs->G, kBThreads, s, (const float*)bs->Q, len,
+  return kl(h, mcgs2_pass_kernel<R, KMAX, KIND>, mpass_grid<R, KMAX, KIND>(h), kBThreads, s,
+            (const float*)bs->Q, len,
             ncol, bs->w, (const double*)bs->h1, (const double*)bs->h2, wout, bs->partials,
             gpart_of(bs), bs->counter, out, bs->H, bs->m + 1, bs->cs, bs->sn, bs->t, bs->st,
             bs->runs, next);
