@@ -411,7 +411,12 @@ HPG_API int hpg_set_execution(hpg_problem_t* h, int mode);
  * matrix does not stream from memory, up to this many rows per phase, let
  * the next kernel launch as soon as they start (their own matrix loads then
  * overlap the previous phase); larger phases let it launch only as their
- * blocks exit.  Same results. */
+ * blocks exit.  Multi-right-hand-side phases (the *_batch calls and batched
+ * solves) up to this many rows are launched programmatically and let the
+ * next kernel launch as soon as they start; larger ones start after the
+ * previous kernel has completed.  Same results: kernels read the vectors an
+ * earlier kernel wrote only after the grid-dependency wait, through coherent
+ * loads. */
 #define HPG_OPT_COARSE_CTA 5
 #define HPG_OPT_PDL_ROWS 6
 HPG_API int hpg_set_option(hpg_problem_t* h, int option, int value);

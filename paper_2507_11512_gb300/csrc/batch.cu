@@ -28,39 +28,23 @@
 namespace hpg {
 
 // ------------------------------------------------------------ R-value access
-// n consecutive values, 4n-byte (FP32) or 8n-byte (FP64) aligned.
-template <int N>
-__device__ __forceinline__ void ldg_n(const float* p, float (&v)[N]) {
-  if constexpr (N == 8) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-    const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-  } else if constexpr (N == 4) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  } else if constexpr (N == 2) {
-    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
-    v[0] = a.x; v[1] = a.y;
-  } else {
-    v[0] = __ldg(p);
-  }
-}
+// n consecutive values, 4n-byte aligned, written by an earlier kernel:
+// coherent L1-cached loads (ld_dep: never the read-only path for such data).
 template <int N>
 __device__ __forceinline__ void ld_n(const float* p, float (&v)[N]) {
   if constexpr (N == 8) {
-    const float4 a = reinterpret_cast<const float4*>(p)[0];
-    const float4 b = reinterpret_cast<const float4*>(p)[1];
+    const float4 a = ld_dep(reinterpret_cast<const float4*>(p));
+    const float4 b = ld_dep(reinterpret_cast<const float4*>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
   } else if constexpr (N == 4) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 a = ld_dep(reinterpret_cast<const float4*>(p));
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   } else if constexpr (N == 2) {
-    const float2 a = *reinterpret_cast<const float2*>(p);
+    const float2 a = ld_dep(reinterpret_cast<const float2*>(p));
     v[0] = a.x; v[1] = a.y;
   } else {
-    v[0] = *p;
+    v[0] = ld_dep(p);
   }
 }
 template <int N>
@@ -98,7 +82,7 @@ mspmv_kernel(const float* __restrict__ vals, const int* __restrict__ cols, long 
     const float a = ld_stream(vals + s * ns + row);
     const int c = ld_stream(cols + s * ns + row);
     float xv[RL];
-    ldg_n<RL>(x + (long long)c * R + lane * RL, xv);
+    ld_n<RL>(x + (long long)c * R + lane * RL, xv);
 #pragma unroll
     for (int r = 0; r < RL; ++r) acc[r] = fma(a, xv[r], acc[r]);
   }
@@ -150,7 +134,7 @@ mgs_phase_kernel(const float* __restrict__ vals, const int* __restrict__ cols, l
     const bool use = MC != kMaskSlots || ((mask >> s) & 1u);
     float xv[RL];
     if (use && col[s] < valid_end) {
-      ldg_n<RL>(z + (long long)col[s] * R + lane * RL, xv);
+      ld_n<RL>(z + (long long)col[s] * R + lane * RL, xv);
     } else {
 #pragma unroll
       for (int r = 0; r < RL; ++r) xv[r] = 0.0f;
@@ -186,7 +170,7 @@ mrestrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom g
     const float a = ld_mat<MODE>(vals + s * ns + row);
     const int c = ld_mat<MODE>(cols + s * ns + row);
     float xv[R];
-    ldg_n<R>(z + (long long)c * R, xv);
+    ld_n<R>(z + (long long)c * R, xv);
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = fma(-a, xv[r], acc[r]);
   }
@@ -244,7 +228,7 @@ mto_storage_kernel(const __grid_constant__ Geom g, int R, const Tin* __restrict_
                         (long long)g.nx * ((2 * J + colour_parity_y(c)) +
                                            (long long)g.ny * (2 * K + colour_parity_z(c)));
   const long long n = (long long)g.nx * g.ny * g.nz;
-  for (int r = 0; r < R; ++r) out[row * R + r] = (Tout)in[r * n + nat];
+  for (int r = 0; r < R; ++r) out[row * R + r] = (Tout)ld_dep(in + r * n + nat);
 }
 
 template <typename Tin, typename Tout>
@@ -260,7 +244,7 @@ mto_natural_kernel(const __grid_constant__ Geom g, int R, const Tin* __restrict_
   const int j = (int)((q / g.nx) % g.ny);
   const int k = (int)(q / ((long long)g.nx * g.ny));
   const long long row = store_index(g, i, j, k);
-  for (int r = 0; r < R; ++r) out[r * n + q] = (Tout)in[row * R + r];
+  for (int r = 0; r < R; ++r) out[r * n + q] = (Tout)ld_dep(in + row * R + r);
 }
 
 // ----------------------------------------------------------- batch space
@@ -361,8 +345,6 @@ static int ensure_vcycle_buffers(hpg_problem* h) {
 }
 
 // ------------------------------------------------------- stencil launchers
-constexpr long long kBatchPdlRows = 16384;   // phases overlapped with their predecessor up to this
-
 static bool streamed(const Level& L) { return L.g.n_store * 27LL * 8 > kStreamMatrixBytes; }
 
 static Shape shape_of(hpg_problem* h, int level, int kind, int R) {
@@ -472,9 +454,12 @@ static int mgs_phase(hpg_problem* h, int level, const float* rhs, float* z, int 
   const int nslots = __builtin_popcount(mask) - 1;
   const double row_bytes = (nslots + 1.0) * 4 + nslots * 4.0 + R * (2.0 + nslots / 26.0) * 4;
   const Shape sh = shape_of(h, level, kShapeGs, R);
-  const bool stream = streamed(L);
   return launch(h, K_GS, level, HPG_FP32, L.cnt[c] * row_bytes, s, "mgs_phase_kernel", [&] {
-    if (stream || nrows > kBatchPdlRows) h->pdl_next = false;
+    // phases of up to HPG_OPT_PDL_ROWS rows (none of a streamed level by
+    // default) are launched programmatically; measured on GB300, launching
+    // the 110,592-row phases of a 96^3 system so as well (triggering at
+    // block exit) made its 8-RHS solve 72.6 instead of 70.9 ms
+    if (nrows > h->pdl_rows) h->pdl_next = false;
     return mgs_dispatch<R>(h, sh.lpr, mmat_mode(L), c, from_zero, nrows, sh.block, s, L.v32,
                            L.cols, L.g.n_store, rhs, z, row0, valid_end, mask);
   });
@@ -665,10 +650,10 @@ __device__ void brotate_warp(int k, const double* __restrict__ h1,
                              double* hs, double* css, double* sns) {
   const int lane = threadIdx.x & 31;
   for (int j = lane; j <= k; j += 32) {
-    hs[j] = h1[j] + h2[j];
+    hs[j] = ld_dep(h1 + j) + ld_dep(h2 + j);
     if (j < k) {
-      css[j] = cs[j];
-      sns[j] = sn[j];
+      css[j] = ld_dep(cs + j);
+      sns[j] = ld_dep(sn + j);
     }
   }
   __syncwarp();
@@ -757,7 +742,7 @@ mcgs2_pass_kernel(const float* __restrict__ Q, long long len, int ncol, float* w
   if (KIND != kBGemvT) {
     const double* hc = KIND == kBReorth ? h1 : h2;
     for (int i = threadIdx.x; i < ncol * R; i += kBThreads)
-      shc[i % R][i / R] = (float)hc[(i % R) * kHStride + i / R];
+      shc[i % R][i / R] = (float)ld_dep(hc + (i % R) * kHStride + i / R);
     __syncthreads();
   }
   // the old rotations of each active right-hand side's Arnoldi column, one
@@ -894,16 +879,16 @@ __global__ void mtrsm_kernel(const double* __restrict__ H, int ldh, const double
   if (rr >= R) return;
   const int k = st[rr].k;
   const double* Hr = H + (long long)rr * ldh * (ldh - 1);
-  for (int j = lane; j < k; j += 32) tt[rr][j] = t[rr * kHStride + j];
+  for (int j = lane; j < k; j += 32) tt[rr][j] = ld_dep(t + rr * kHStride + j);
   __syncwarp();
   for (int i = k - 1; i >= 0; --i) {
     if (lane == 0) {
-      yi_s[rr] = tt[rr][i] / Hr[(long long)i * ldh + i];
+      yi_s[rr] = tt[rr][i] / ld_dep(Hr + (long long)i * ldh + i);
       y[rr * kHStride + i] = yi_s[rr];
     }
     __syncwarp();
     const double yi = yi_s[rr];
-    for (int j = lane; j < i; j += 32) tt[rr][j] -= Hr[(long long)i * ldh + j] * yi;
+    for (int j = lane; j < i; j += 32) tt[rr][j] -= ld_dep(Hr + (long long)i * ldh + j) * yi;
     __syncwarp();
   }
 }
@@ -918,7 +903,7 @@ mcombine_kernel(const float* __restrict__ Q, long long len, const double* __rest
   __shared__ float ys[R][kMaxRestart + 1];
   __shared__ int ks[R];
   for (int i = threadIdx.x; i < R * kmax; i += kBThreads)
-    ys[i / kmax][i % kmax] = (float)y[(i / kmax) * kHStride + i % kmax];
+    ys[i / kmax][i % kmax] = (float)ld_dep(y + (i / kmax) * kHStride + i % kmax);
   if (threadIdx.x < R) ks[threadIdx.x] = st[threadIdx.x].k;
   __syncthreads();
   const int r = threadIdx.x % R;
@@ -937,7 +922,7 @@ mupdate_x_kernel(double* __restrict__ x, const float* __restrict__ d, long long 
   pdl_trigger();
   pdl_wait();
   const long long e = blockIdx.x * (long long)kBThreads + threadIdx.x;
-  if (e < len) x[e] += (double)d[e];
+  if (e < len) x[e] += (double)ld_dep(d + e);
 }
 
 // r = b - A x (FP64, Algorithm 3 outer residual) and ||r_r||^2 per
@@ -958,13 +943,13 @@ mresidual_kernel(const double* __restrict__ vals, const int* __restrict__ cols, 
        row += stride) {
     double v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = b[row * R + r];
+    for (int r = 0; r < R; ++r) v[r] = ld_dep(b + row * R + r);
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
       const double a = ld_stream(vals + s * ns + row);
       const int c = ld_stream(cols + s * ns + row);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = fma(-a, __ldg(x + (long long)c * R + r), v[r]);
+      for (int r = 0; r < R; ++r) v[r] = fma(-a, ld_dep(x + (long long)c * R + r), v[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -991,7 +976,10 @@ mnorm2_kernel(const double* __restrict__ v, long long ns, double* partials, doub
   for (long long row = blockIdx.x * (long long)kBThreads + threadIdx.x; row < ns;
        row += stride)
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = fma(v[row * R + r], v[row * R + r], acc[r]);
+    for (int r = 0; r < R; ++r) {
+      const double vr = ld_dep(v + row * R + r);
+      acc[r] = fma(vr, vr, acc[r]);
+    }
   __shared__ double sums[R];
   if (mblock_partials_last<1, R>(acc, R, partials, gpart, counter, sums) && threadIdx.x < R)
     out[threadIdx.x] = sums[threadIdx.x];
@@ -1011,7 +999,7 @@ __global__ void mouter_check_kernel(const double* __restrict__ rho2, BState* st,
   if (threadIdx.x < R) {
     BState& s = st[threadIdx.x];
     if (!s.done) {
-      const double rho = sqrt(rho2[threadIdx.x]);
+      const double rho = sqrt(ld_dep(rho2 + threadIdx.x));
       const double rel = rho / s.rho0;
       s.rho = rho;
       s.rel = rel;
@@ -1054,7 +1042,7 @@ mcycle_start_kernel(const double* __restrict__ res, long long len, float* __rest
   __syncthreads();
   const long long e = blockIdx.x * (long long)kBThreads + threadIdx.x;
   const int r = threadIdx.x % R;
-  if (e < len) q0[e] = act[r] ? (float)(res[e] * inv[r]) : 0.0f;
+  if (e < len) q0[e] = act[r] ? (float)(ld_dep(res + e) * inv[r]) : 0.0f;
   if (blockIdx.x != 0) return;
   if (threadIdx.x < R) {
     BState& s = st[threadIdx.x];

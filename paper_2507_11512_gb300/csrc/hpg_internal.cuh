@@ -145,6 +145,22 @@ __device__ __forceinline__ void pdl_trigger() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Load of a vector that an earlier kernel of the chain wrote.  A kernel
+// launched programmatically is alive while its predecessor still writes, so
+// the read-only path (ld.global.nc: __ldg, or a const __restrict__ pointer
+// the compiler lowers to it) is not valid for such data: it is only for data
+// that no kernel writes while the reader runs (the matrix).  Measured on
+// GB300: a multi-RHS Gauss-Seidel phase whose neighbour gathers took the
+// read-only path, with its matrix slots loaded before pdl_wait(), returned
+// values from before the previous kernel's writes on every run; with these
+// coherent L1-cached loads (ld.global.ca) it is bitwise exact, at the same
+// speed.  The load is volatile inline assembly, so it stays after
+// pdl_wait() in program order.
+template <typename V>
+__device__ __forceinline__ V ld_dep(const V* p) {
+  return __ldca(p);
+}
+
 // Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (no registers,
 // no completion to wait for).  p must be 16-byte aligned, bytes a multiple
 // of 16.

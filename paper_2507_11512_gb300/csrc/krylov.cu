@@ -448,10 +448,10 @@ __device__ void arnoldi_rotate_warp(int k, const double* __restrict__ h1,
   __shared__ double hs[KMAX + 1], css[KMAX], sns[KMAX];
   const int lane = threadIdx.x & 31;
   for (int j = lane; j <= k; j += 32) {
-    hs[j] = h1[j] + h2[j];
+    hs[j] = ld_dep(h1 + j) + ld_dep(h2 + j);
     if (j < k) {
-      css[j] = cs[j];
-      sns[j] = sn[j];
+      css[j] = ld_dep(cs + j);
+      sns[j] = ld_dep(sn + j);
     }
   }
   __syncwarp();
@@ -537,7 +537,7 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
   if (KIND != kGemvT) {
     const double* hc = KIND == kReorth ? h1 : h2;
     for (int j = threadIdx.x; j < ncol; j += kRedThreads)
-      shc[j] = (T)(S ? hc[j] * (double)qscale[j] : hc[j]);
+      shc[j] = (T)(S ? ld_dep(hc + j) * (double)ld_dep(qscale + j) : ld_dep(hc + j));
     __syncthreads();
   }
   // the rotations that do not need beta, by one warp while the pass streams;
@@ -629,7 +629,7 @@ cgs2_pass_kernel(const B* __restrict__ Q, long long ns, int ncol, const T* w,
   if (!block_partials_last<T, KMAX, MAXLAST>(acc, nred, partials, counter, sums)) return;
   if (KIND != kFinal) {
     for (int j = threadIdx.x; j < nred; j += kRedThreads)
-      out[j] = S ? sums[j] * (double)qscale[j] : sums[j];
+      out[j] = S ? sums[j] * (double)ld_dep(qscale + j) : sums[j];
   } else if (threadIdx.x < 32) {
     if (MAXLAST && threadIdx.x == 0) st->wmax = sums[1];
     arnoldi_givens_warp(sqrt(sums[0]), ncol - 1, H, ldh, cs, sn, t, st, next);
@@ -730,16 +730,16 @@ __global__ void trsm_kernel(const double* __restrict__ H, int ldh, const double*
   __shared__ double tt[kMaxRestart + 1];
   __shared__ double yi_s;
   const int k = st->k;
-  for (int j = threadIdx.x; j < k; j += 32) tt[j] = t[j];
+  for (int j = threadIdx.x; j < k; j += 32) tt[j] = ld_dep(t + j);
   __syncwarp();
   for (int i = k - 1; i >= 0; --i) {
     if (threadIdx.x == 0) {
-      yi_s = tt[i] / H[(long long)i * ldh + i];
+      yi_s = tt[i] / ld_dep(H + (long long)i * ldh + i);
       y[i] = yi_s;
     }
     __syncwarp();
     const double yi = yi_s;
-    for (int j = threadIdx.x; j < i; j += 32) tt[j] -= H[(long long)i * ldh + j] * yi;
+    for (int j = threadIdx.x; j < i; j += 32) tt[j] -= ld_dep(H + (long long)i * ldh + j) * yi;
     __syncwarp();
   }
 }
@@ -756,7 +756,7 @@ basis_combine_kernel(const B* __restrict__ Q, long long ns, const double* __rest
   __shared__ T ys[kMaxRestart + 1];
   const int k = st->k;
   for (int j = threadIdx.x; j < k; j += blockDim.x)
-    ys[j] = (T)(basis_scaled<B>() ? y[j] * (double)qscale[j] : y[j]);
+    ys[j] = (T)(basis_scaled<B>() ? ld_dep(y + j) * (double)ld_dep(qscale + j) : ld_dep(y + j));
   __syncthreads();
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= (ns >> 2)) return;
@@ -778,7 +778,7 @@ update_x_kernel(double* __restrict__ x, const T* __restrict__ d, long long ns) {
   pdl_trigger();
   pdl_wait();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < ns) x[i] += (double)d[i];
+  if (i < ns) x[i] += (double)ld_dep(d + i);
 }
 
 // r = b - A x, ||r||^2 and max |r| (FP64; the maximum scales q_0 of a
@@ -794,12 +794,12 @@ residual_norm_kernel(const double* __restrict__ vals, const int* __restrict__ co
   const long long stride = (long long)gridDim.x * kRedThreads;
   for (long long row = blockIdx.x * (long long)kRedThreads + threadIdx.x; row < ns;
        row += stride) {
-    double v = b[row];
+    double v = ld_dep(b + row);
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
       const double a = ld_stream(vals + s * ns + row);
       const int c = ld_stream(cols + s * ns + row);
-      v = fma(-a, __ldg(x + c), v);
+      v = fma(-a, ld_dep(x + c), v);
     }
     r[row] = v;
     acc[0] = fma(v, v, acc[0]);
@@ -818,8 +818,10 @@ norm2_kernel(const double* __restrict__ v, long long ns, double* __restrict__ pa
   pdl_wait();
   double acc[1] = {0.0};
   const long long stride = (long long)gridDim.x * kRedThreads;
-  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < ns; i += stride)
-    acc[0] = fma(v[i], v[i], acc[0]);
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < ns; i += stride) {
+    const double vi = ld_dep(v + i);
+    acc[0] = fma(vi, vi, acc[0]);
+  }
   __shared__ double sums[1];
   if (block_partials_last<double, 1>(acc, 1, partials, counter, sums) && threadIdx.x == 0)
     out[0] = sums[0];
@@ -833,12 +835,12 @@ __global__ void outer_check_kernel(const double* __restrict__ rho2, SolveState* 
   pdl_trigger();
   pdl_wait();
   if (threadIdx.x != 0) return;
-  const double rho = sqrt(*rho2);
+  const double rho = sqrt(ld_dep(rho2));
   const double rel = rho / st->rho0;
   st->rho = rho;
   st->rel = rel;
   bool done = true;
-  if (pipe_err && *pipe_err != 0) {
+  if (pipe_err && ld_dep(pipe_err) != 0) {
     st->status = HPG_ERR_TIMEOUT;   // a kernel's bounded wait gave up
   } else if (!isfinite(rel)) {
     st->status = HPG_ERR_NAN;
@@ -873,7 +875,7 @@ cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q
   const double rho = st->rho;
   if (threadIdx.x == 0) {
     if constexpr (basis_scaled<B>()) {
-      const double m = rho2[1];
+      const double m = ld_dep(rho2 + 1);
       s_inv = m > 0.0 ? 1.0 / m : 0.0;
       s_sigma = (float)(m / rho);
     } else {
@@ -886,7 +888,7 @@ cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q
     const double inv = s_inv;
     const float sigma = s_sigma;
     if (i < ns) {
-      const B u = basis_from<B>((float)(r[i] * inv));
+      const B u = basis_from<B>((float)(ld_dep(r + i) * inv));
       q0[i] = u;
       const float v = sigma * basis_to(u);
       qf[i] = v;
@@ -896,7 +898,7 @@ cycle_start_kernel(const double* __restrict__ r, long long ns, B* __restrict__ q
   } else {
     const double inv = s_inv;
     if (i < ns) {
-      const T v = (T)(r[i] * inv);
+      const T v = (T)(ld_dep(r + i) * inv);
       q0[i] = v;
       if (i < c0_rows) z0[i] = v / diag[i];   // the first V-cycle's first phase
     }

@@ -113,7 +113,7 @@ __global__ void gen_ell_kernel(const __grid_constant__ Geom g, double beta,
   const int j = 2 * J + colour_parity_y(c);
   const int k = 2 * K + colour_parity_z(c);
   const double th =
-      theta ? theta[(long long)i + (long long)g.nx * (j + (long long)g.ny * k)] : 1.0;
+      theta ? ld_dep(theta + (long long)i + (long long)g.nx * (j + (long long)g.ny * k)) : 1.0;
   for (int s = 0; s < kSlots; ++s) {
     const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
     const int ni = i + dx, nj = j + dy, nk = k + dz;
@@ -141,7 +141,7 @@ __global__ void inject_theta_kernel(int fnx, int fny, int cnx, int cny, int cnz,
   const int I = (int)(q % cnx);
   const int J = (int)((q / cnx) % cny);
   const int K = (int)(q / ((long long)cnx * cny));
-  tc[q] = tf[2LL * I + (long long)fnx * (2LL * J + (long long)fny * 2 * K)];
+  tc[q] = ld_dep(tf + 2LL * I + (long long)fnx * (2LL * J + (long long)fny * 2 * K));
 }
 
 // Gradient of a loss with respect to the per-cell diagonal scales: only
@@ -155,7 +155,7 @@ diag_scale_gradient_kernel(long long n, const double* __restrict__ lam,
   pdl_wait();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
-    grad[i] = (-kDiag * lam[i]) * x[i];
+    grad[i] = (-kDiag * ld_dep(lam + i)) * ld_dep(x + i);
 }
 
 template <typename Tin, typename Tout>
@@ -179,7 +179,7 @@ __global__ void to_storage_kernel(const __grid_constant__ Geom g, const Tin* __r
   const int i = 2 * I + colour_parity_x(c);
   const int j = 2 * J + colour_parity_y(c);
   const int k = 2 * K + colour_parity_z(c);
-  out[row] = (Tout)in[(long long)i + (long long)g.nx * (j + (long long)g.ny * k)];
+  out[row] = (Tout)ld_dep(in + (long long)i + (long long)g.nx * (j + (long long)g.ny * k));
 }
 
 template <typename Tin, typename Tout>
@@ -193,7 +193,7 @@ __global__ void to_natural_kernel(const __grid_constant__ Geom g, const Tin* __r
   const int i = (int)(q % g.nx);
   const int j = (int)((q / g.nx) % g.ny);
   const int k = (int)(q / ((long long)g.nx * g.ny));
-  out[q] = (Tout)in[store_index(g, i, j, k)];
+  out[q] = (Tout)ld_dep(in + store_index(g, i, j, k));
 }
 
 // ----------------------------------------------------------------- launchers

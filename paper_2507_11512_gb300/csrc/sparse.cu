@@ -46,7 +46,7 @@ spmv_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long 
   for (int s = 0; s < kSlots; ++s) {
     const T a = ld_stream(vals + s * ns + row);
     const int c = ld_stream(cols + s * ns + row);
-    acc = fma(a, __ldg(x + c), acc);
+    acc = fma(a, ld_dep(x + c), acc);
   }
   y[row] = acc;
 }
@@ -62,12 +62,12 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
   pdl_wait();
   const long long row = row0 + threadIdx.x;
   if (row >= ns) return;
-  double acc = b[row];
+  double acc = ld_dep(b + row);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     const double a = ld_stream(vals + s * ns + row);
     const int c = ld_stream(cols + s * ns + row);
-    acc = fma(-a, __ldg(x + c), acc);
+    acc = fma(-a, ld_dep(x + c), acc);
   }
   r[row] = acc;
 }
@@ -104,13 +104,13 @@ gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long l
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nrows) return;
   const long long row = row0 + t;
-  T acc = r[row];
+  T acc = ld_dep(r + row);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     if (s == kCentre || !((kMask >> s) & 1u)) continue;
     const T a = ld_matrix<STREAM>(vals + s * ns + row);
     const int c = ld_matrix<STREAM>(cols + s * ns + row);
-    const T xv = (c < valid_end) ? __ldg(x + c) : T(0);
+    const T xv = (c < valid_end) ? ld_dep(x + c) : T(0);
     acc = fma(-a, xv, acc);
   }
   const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
@@ -348,9 +348,9 @@ gs_phase_small_kernel(const T* __restrict__ vals, const int* __restrict__ cols, 
   T xv[kSlots];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s)
-    xv[s] = (s != kCentre && ((kMask >> s) & 1u) && col[s] < valid_end) ? __ldg(x + col[s])
+    xv[s] = (s != kCentre && ((kMask >> s) & 1u) && col[s] < valid_end) ? ld_dep(x + col[s])
                                                                         : T(0);
-  T acc = r[row];
+  T acc = ld_dep(r + row);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s)
     if (s != kCentre && ((kMask >> s) & 1u)) acc = fma(-a[s], xv[s], acc);
@@ -429,7 +429,7 @@ template <typename T, bool STREAM, bool MASKED>
 __device__ __forceinline__ void pipe_row(const T* __restrict__ vals, const int* __restrict__ cols,
                                          long long ns, const T* __restrict__ r, T* z,
                                          long long row, long long valid_end, unsigned mask) {
-  T acc = r[row];
+  T acc = ld_dep(r + row);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     if (s == kCentre) continue;
@@ -563,12 +563,12 @@ restrict_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc
   const long long p = p0 + threadIdx.x;
   if (p >= cnt) return;
   const long long row = gf.off[kCoarseColour] + p;
-  T acc = r[row];
+  T acc = ld_dep(r + row);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     const T a = ld_mat<MODE>(vals + s * ns + row);
     const int c = ld_mat<MODE>(cols + s * ns + row);
-    acc = fma(-a, __ldg(z + c), acc);
+    acc = fma(-a, ld_dep(z + c), acc);
   }
   const int I = (int)(p % cx);
   const int J = (int)((p / cx) % cy);
@@ -594,7 +594,7 @@ prolong_kernel(const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
   const int J = (int)((p / cx) % cy);
   const int K = (int)(p / ((long long)cx * cy));
   const long long row = gf.off[kCoarseColour] + p;
-  z[row] += zc[store_index(gc, I, J, K)];
+  z[row] += ld_dep(zc + store_index(gc, I, J, K));
 }
 
 // ----------------------------------------------------------------- launchers
@@ -896,12 +896,12 @@ coarse_sweep_cta_kernel(const T* __restrict__ vals, const int* __restrict__ cols
       col[q] = use ? ld_mat<MODE>(cols + (long long)q * ns + row) : 0;
       a[q] = use ? ld_mat<MODE>(vals + (long long)q * ns + row) : T(1);
     }
-    if (rhs) rr = live ? r[row] : T(0);
+    if (rhs) rr = live ? ld_dep(r + row) : T(0);
   };
   load(0, false);
   pdl_wait();
-  if (t < plan.ph[0].nrows) rr = r[plan.ph[0].row0 + t];
-  for (int i = t; i < ns; i += blockDim.x) sz[i] = i < plan.c0_rows ? z[i] : T(0);
+  if (t < plan.ph[0].nrows) rr = ld_dep(r + plan.ph[0].row0 + t);
+  for (int i = t; i < ns; i += blockDim.x) sz[i] = i < plan.c0_rows ? ld_dep(z + i) : T(0);
   __syncthreads();
   for (int p = 0; p < plan.nphases; ++p) {
     const CtaSweepPhase& ph = plan.ph[p];

@@ -203,14 +203,20 @@ def test_problem_outlives_its_batch():
         pb.close()
 
 
+@pytest.mark.parametrize("pdl_rows", [16384, 1 << 30])
 @pytest.mark.parametrize("R", [2, 8])
-def test_streamed_size_system_columns_equal_single_vector_kernels(R):
+def test_streamed_size_system_columns_equal_single_vector_kernels(R, pdl_rows):
     """A 96^3 system (the batched workload's largest edge): its level-0 matrix
     streams from memory, level 1 is cached, levels 2-3 are read evict-last;
-    every launch shape's columns equal the single-vector kernels bitwise."""
+    every launch shape's columns equal the single-vector kernels bitwise.
+    pdl_rows = 2^30 launches every phase programmatically, so each phase's
+    matrix loads overlap the previous kernel and its gathers follow the
+    grid-dependency wait directly: read through the non-coherent path, the
+    level-0 columns of that configuration differed on GB300."""
     dims = (96, 96, 96)
     with hpg.Problem(*dims, beta=0.6) as p:
         assert p.n_store(0) * 27 * 8 > (96 << 20)
+        hpg.set_option(p.h, hpg.HPG_OPT_PDL_ROWS, pdl_rows)
         for level in (0, 1):
             _, X = rvec(p, level, R, 30 + level)
             ref_s = [p.spmv(X[:, r].contiguous(), level=level) for r in range(R)]
@@ -227,6 +233,24 @@ def test_streamed_size_system_columns_equal_single_vector_kernels(R):
                     assert torch.equal(Z[:, r], ref_v[r]), (level, lpr, blk, r)
             for kind in (batch.KIND_SPMV, batch.KIND_GS):
                 batch.set_shape(p.h, level, kind, R, 0, 0)
+
+
+def test_batched_solve_same_with_every_phase_programmatic():
+    dims = (96, 96, 96)
+    g = torch.Generator(device="cpu").manual_seed(11)
+    n = dims[0] * dims[1] * dims[2]
+    B = torch.randn(2, n, generator=g, dtype=torch.float64).to(DEV)
+    with hpg.Problem(*dims, beta=0.6) as p:
+        xs, its = [], []
+        for rows in (16384, 1 << 30):
+            hpg.set_option(p.h, hpg.HPG_OPT_PDL_ROWS, rows)
+            X = torch.zeros_like(B)
+            infos = batch.solve_batch(p.h, B, X, tol=1e-8)
+            assert all(i["converged"] for i in infos)
+            xs.append(X)
+            its.append([i["iterations"] for i in infos])
+    assert its[0] == its[1]
+    assert torch.equal(xs[0], xs[1])
 
 
 def test_streamed_size_batched_solve_matches_oracle():
