@@ -149,7 +149,8 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // launched programmatically is alive while its predecessor still writes, so
 // the read-only path (ld.global.nc: __ldg, or a const __restrict__ pointer
 // the compiler lowers to it) is not valid for such data: it is only for data
-// that no kernel writes while the reader runs (the matrix).  Measured on
+// that no kernel writes while the reader runs (the matrix, or the input of a
+// kernel that is never launched programmatically).  Measured on
 // GB300: a multi-RHS Gauss-Seidel phase whose neighbour gathers took the
 // read-only path, with its matrix slots loaded before pdl_wait(), returned
 // values from before the previous kernel's writes on every run; with these
