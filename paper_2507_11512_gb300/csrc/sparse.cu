@@ -72,6 +72,38 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
   r[row] = acc;
 }
 
+// Rows a thread of a bandwidth-variant Gauss-Seidel phase takes, and the
+// 16-byte vector types that load one slot of them at once.
+template <typename T> struct PhaseRows;
+template <> struct PhaseRows<float> {
+  static constexpr int R = 4;
+  using V = float4;
+  using I = int4;
+};
+template <> struct PhaseRows<double> {
+  static constexpr int R = 2;
+  using V = double2;
+  using I = int2;
+};
+__device__ __forceinline__ void split_rows(const float4& v, float (&o)[4]) {
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void split_rows(const double2& v, double (&o)[2]) {
+  o[0] = v.x; o[1] = v.y;
+}
+__device__ __forceinline__ float4 join_rows(const float (&o)[4]) {
+  return make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ double2 join_rows(const double (&o)[2]) {
+  return make_double2(o[0], o[1]);
+}
+__device__ __forceinline__ void split_rows(const int4& v, int (&o)[4]) {
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void split_rows(const int2& v, int (&o)[2]) {
+  o[0] = v.x; o[1] = v.y;
+}
+
 // One Gauss-Seidel colour phase (Sec. 3.2.1, relaxation form of eq. (1)):
 // for every row i of the colour block [row0, row0 + nrows),
 //   x_i <- (r_i - sum_{j != i} a_ij x_j) / a_ii.
@@ -80,9 +112,22 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
 // sweep from z = 0 passes valid_end = start of the current colour block, so
 // that colours not yet visited count as zero without a memset.
 //
-// Bandwidth variant, for levels whose matrix streams from HBM: 32 registers,
-// eight 256-thread CTAs per SM (a 128^3 colour phase is a single wave), the
-// matrix read evict-first.  No early trigger and no load before the
+// Bandwidth variant, for levels whose matrix streams from HBM: a thread takes
+// PhaseRows<T>::R consecutive rows and loads each slot's values and indices
+// for them as one 16-byte vector (the colour blocks start and end on 32-row
+// boundaries, so the rows divide evenly and the loads are aligned), and r
+// and x likewise: the launcher sends vectors off a 16-byte boundary (caller
+// pointers) to the one-row-per-thread latency kernel instead, whose per-row
+// arithmetic is the same (a branch on the alignment inside this kernel cost
+// 1 %).  Each row's
+// arithmetic is the one-row-per-thread kernel's, in the same order.  Two
+// 256-thread CTAs per SM with 128 registers, so a thread has its rows' loads
+// in flight at once (a 128^3 FP32 phase is 256 CTAs, one wave).  Measured on
+// GB300 against one row per thread in 32 registers (8 CTAs per SM): level-0
+// phase 10.72 -> 9.35 us, 128^3 solve 102.8 -> 97.4 ms, 320^3 3534 ->
+// 3401 ms; 2 rows per thread in 64 registers 99.7 ms, 4 rows in 64 or 80
+// registers 103.0 / 101.9 ms, 4 rows in 128-thread CTAs 97.7 ms.  The
+// matrix is read evict-first.  No early trigger and no load before the
 // programmatic wait: measured on GB300, letting the next phase's CTAs start
 // early (or prefetching its slots into L2) slows this bandwidth-bound chain
 // down; launched with the programmatic attribute but triggering only as its
@@ -95,26 +140,38 @@ residual64_kernel(const double* __restrict__ vals, const int* __restrict__ cols,
 // run-time slot mask made these phases no faster than full ones on GB300
 // (colour 0, which loads only the diagonal, took 70 % of a full phase).
 template <typename T, bool STREAM, int MC>
-__global__ void __launch_bounds__(256, 8)
+__global__ void __launch_bounds__(256, 2)
 gs_phase_kernel(const T* __restrict__ vals, const int* __restrict__ cols, long long ns,
                 const T* __restrict__ r, T* x, long long row0, long long nrows,
                 long long valid_end) {
   constexpr unsigned kMask = MC < 0 ? (1u << kSlots) - 1u : gs_slot_mask(MC, true);
+  constexpr int NR = PhaseRows<T>::R;
+  using V = typename PhaseRows<T>::V;
+  using I = typename PhaseRows<T>::I;
   pdl_wait();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nrows) return;
-  const long long row = row0 + t;
-  T acc = ld_dep(r + row);
+  if (NR * t >= nrows) return;
+  const long long row = row0 + NR * t;
+  T acc[NR];
+  split_rows(ld_dep(reinterpret_cast<const V*>(r + row)), acc);
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     if (s == kCentre || !((kMask >> s) & 1u)) continue;
-    const T a = ld_matrix<STREAM>(vals + s * ns + row);
-    const int c = ld_matrix<STREAM>(cols + s * ns + row);
-    const T xv = (c < valid_end) ? ld_dep(x + c) : T(0);
-    acc = fma(-a, xv, acc);
+    T a[NR];
+    int c[NR];
+    split_rows(ld_matrix<STREAM>(reinterpret_cast<const V*>(vals + s * ns + row)), a);
+    split_rows(ld_matrix<STREAM>(reinterpret_cast<const I*>(cols + s * ns + row)), c);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const T xv = (c[q] < valid_end) ? ld_dep(x + c[q]) : T(0);
+      acc[q] = fma(-a[q], xv, acc[q]);
+    }
   }
-  const T diag = ld_matrix<STREAM>(vals + kCentre * ns + row);
-  x[row] = acc / diag;
+  T diag[NR];
+  split_rows(ld_matrix<STREAM>(reinterpret_cast<const V*>(vals + kCentre * ns + row)), diag);
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = acc[q] / diag[q];
+  *reinterpret_cast<V*>(x + row) = join_rows(acc);
 }
 
 // The bandwidth-variant instantiation of a phase of colour c.
@@ -736,6 +793,10 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                     // phase never triggers early and waits before its first load
                     // (see gs_phase_kernel): the next phase's launch is set up while
                     // this one drains; measured 103.6 -> 102.9 ms at 128^3
+                    if (((uintptr_t)r | (uintptr_t)z) & 15u)   // see gs_phase_kernel
+                      return kl(h, gs_small_fn<T>(kMatCached, c, from_zero),
+                                grid_for(nrows, small_threads<T>()), small_threads<T>(), s,
+                                vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end, 0);
                     cudaError_t he = cudaSuccess;
                     if (!from_zero &&
                         (keep ? launch_gs_halo<T, false>(h, L, r, z, c, s, &he)
@@ -743,11 +804,11 @@ static int gs_phase(hpg_problem* h, int level, const T* r, T* z, int c, bool fro
                       return he;
                     if (keep)   // slice read again soon after: leave it in L2
                       return kl(h, gs_phase_fn<T, false>(c, from_zero),
-                                grid_for(nrows, kThreads), kThreads, s, vals, L.cols,
-                                L.g.n_store, r, z, row0, nrows, valid_end);
-                    return kl(h, gs_phase_fn<T, true>(c, from_zero), grid_for(nrows, kThreads),
-                              kThreads, s, vals, L.cols, L.g.n_store, r, z, row0, nrows,
-                              valid_end);
+                                grid_for(nrows / PhaseRows<T>::R, kThreads), kThreads, s,
+                                vals, L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
+                    return kl(h, gs_phase_fn<T, true>(c, from_zero),
+                              grid_for(nrows / PhaseRows<T>::R, kThreads), kThreads, s, vals,
+                              L.cols, L.g.n_store, r, z, row0, nrows, valid_end);
                   }
                   // measured on GB300: programmatic overlap helps the smallest
                   // phases and slows phases of tens of thousands of rows (with
