@@ -193,6 +193,11 @@ static GsPhaseFn<T, STREAM> gs_phase_fn(int c, bool from_zero) {
   }
 }
 
+// A colour block's rows (a multiple of kRowAlign) split evenly into the
+// bandwidth-variant phase's rows per thread.
+static_assert(kRowAlign % PhaseRows<float>::R == 0 && kRowAlign % PhaseRows<double>::R == 0,
+              "colour blocks must split evenly into a thread's rows");
+
 // TMA-tiled variant of the streamed phase (option HPG_OPT_GS_HALO): a CTA
 // takes whole x-lines of its colour block -- lines J0 .. J0+L-1 of plane K --
 // and moves everything its rows read into shared memory with 1-D bulk
