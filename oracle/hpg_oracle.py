@@ -48,6 +48,11 @@ in the design notes of the repository):
 * inner test: the Givens estimate rho = |t_{k+1}| against tau * ||b||.
 * iteration count: the total number of inner (Arnoldi) steps.
 
+Parity unpinned: the flop model (``level_nnz``, ``vcycle_flops``,
+``solve_flops``).  The paper says its flop count is carefully constructed but
+does not print it, so nothing outside this file fixes these counts; the tests
+only check that the library's closed-form count equals them.
+
 The differentiable solve (``dense_adjoint_gradients``) has no counterpart in
 the paper: it is the plain definition of the gradient of a loss through
 A(theta) x = b by the adjoint equation, written with dense LAPACK solves for
@@ -342,7 +347,8 @@ def level_nnz(level):
 
 
 def vcycle_flops(levels, lev=0, pre=1, post=1):
-    """Flops of one V-cycle under the counting model (all precisions equal).
+    """Flops of one V-cycle under the counting model (all precisions equal;
+    parity unpinned: the paper does not print its model).
 
     Gauss-Seidel half sweep: 2 nnz + n (one divide per row);
     fused residual-restriction: 2 nnz of the coarse-coincident fine rows + n_c;
